@@ -1,0 +1,332 @@
+"""Benchmark: objective + gradient evaluations per second on the clinical-size
+scan pair (300 x 300 A-scans x 512 samples, float32, 3-level pyramid), plus
+the full coarse-to-fine solve time per pair.
+
+A step is one objective + gradient evaluation at full resolution through the
+library (displacement -> data term + regulariser + mean term + final
+reductions, f read back on the host).  ``value`` times steps with inputs
+resident in GPU memory; ``e2e`` times the same call with the displacement
+copied in from pinned host memory and the gradient copied back every step.
+The two volumes (368 MB) exceed the 129 MB L2, so every step streams them
+from HBM.  Multi-GPU: independent replicas per rank (the method has no
+exchange step), max time over ranks.
+
+``--impl reference`` times the FP64 CPU oracle on the same workload instead.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "c2"
+METRIC = "objective+grad evals/s (GB/s vs HBM peak), solve time per pair at ≤0.05px RMS"
+FP32_LANES_PER_SM = 128
+N_SM = 152
+
+
+def flops_per_eval(w, h, d):
+    # per voxel and scan: 16 FMA transverse, 4 + 4 axial value/derivative,
+    # 4 + 16 adjoint (x/y gradient); per voxel pair about 8 flops of loss
+    return float(w) * h * d * (2 * 44 * 2 + 8)
+
+
+def bytes_per_eval(w, h, d, s=4):
+    # both volumes once, both en-face images, displacement read, gradient
+    # write, per-A-scan structural/angio partials
+    return float(w) * h * (2 * d * s + 2 * 4 + 6 * 8 + 6 * 8 + 2 * 8)
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend=backend)
+        return dist, rank, ws
+    return None, 0, 1
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region (SM clock, throttle reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_bench_%d.csv" % os.getpid()
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def kernel_traffic(w, h, d):
+    """dram bytes per launch of the data-term kernel from the committed ncu
+    summary, scaled to this workload; None if the kernel source changed."""
+    path = os.path.join(ROOT, "profiles", "data_kernel_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except Exception:
+        return None
+    src = open(os.path.join(ROOT, "paper_2010_06931_gb300", "csrc", "k_data.cu"), "rb").read()
+    if rec.get("k_data_sha1") != hashlib.sha1(src).hexdigest():
+        return None
+    scale = (w * h * d) / float(rec["w"] * rec["h"] * rec["d"])
+    return rec["dram_bytes_per_launch"] * scale
+
+
+def make_workload(name):
+    from octsynth import make_config
+    pair, cfg = make_config(name)
+    return pair, cfg
+
+
+def cpu_baseline(pair, cfg, budget_s=15.0):
+    """The FP64 oracle (as it stands) on host cores: full objective + gradient
+    evaluations of the same level-0 pair, as many as fit in ~budget_s."""
+    import oracle as O
+    P = O.OracleProblem(pair["sx"], pair["sy"], pair["tx"], pair["ty"], pair["ax"], pair["ay"],
+                        pair["vx"], pair["vy"])
+    D = np.random.default_rng(0).normal(0.0, 0.5, P.shape_disp())
+    P.eta = 0.7
+    n, t0 = 0, time.perf_counter()
+    while True:
+        P.eval(D)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or (el / n) * (n + 1) > 2 * budget_s:
+            break
+    return {"value": n / el, "unit": "evals/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": "%d full FP64 objective+gradient evaluations of the %dx%dx%d level-0 pair" %
+                      (n, cfg["w"], cfg["h"], cfg["d"])}
+
+
+def run_reference(args):
+    """Times the oracle on the same metric and workload (rank 0 only)."""
+    import oracle as O
+    _, rank, ws = dist_setup(args)
+    if rank != 0:
+        return
+    pair, cfg = make_workload(args.workload)
+    w, h, d = cfg["w"], cfg["h"], cfg["d"]
+    P = O.OracleProblem(pair["sx"], pair["sy"], pair["tx"], pair["ty"], pair["ax"], pair["ay"],
+                        pair["vx"], pair["vy"])
+    D = np.random.default_rng(0).normal(0.0, 0.5, P.shape_disp())
+    P.eta = 0.7
+    t0 = time.perf_counter()
+    P.data_rows(D, 0, min(h, 8))
+    t_row = (time.perf_counter() - t0) / min(h, 8)
+    # each step: the data term over a sample of rows sized so the run ends in ~2 min
+    rows = int(max(1, min(h, (120.0 / max(args.steps + args.warmup, 1)) / max(t_row, 1e-9))))
+    for s in range(args.warmup):
+        j0 = (s * rows) % max(h - rows + 1, 1)
+        P.data_rows(D, j0, j0 + rows)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        j0 = (s * rows) % max(h - rows + 1, 1)
+        P.data_rows(D, j0, j0 + rows)
+    el = time.perf_counter() - t0
+    evals_per_s = args.steps * rows / h / el
+    sample = "data term of %d of %d rows per step (scaled to whole evaluations)" % (rows, h)
+    line = {"impl": "reference", "metric": METRIC, "value": evals_per_s, "unit": "evals/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "%s: %dx%d A-scans x %d, float32 volumes" % (args.workload, w, h, d)},
+            "cpu_baseline": {"value": evals_per_s, "unit": "evals/s", "cores": O.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": evals_per_s, "unit": "evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    dist, rank, ws = dist_setup(args)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    import paper_2010_06931_gb300 as octmc
+
+    pair, cfg = make_workload(args.workload)
+    w, h, d, levels = cfg["w"], cfg["h"], cfg["d"], cfg["levels"]
+    stream = torch.cuda.current_stream()
+    P = octmc.Problem(pair["sx"], pair["sy"], pair["tx"], pair["ty"], pair["ax"], pair["ay"],
+                      pair["vx"], pair["vy"], levels=levels)
+    rng = np.random.default_rng(rank)
+    D = torch.from_numpy(rng.normal(0.0, 0.5, P.disp_shape(0))).cuda()
+    G = torch.empty_like(D)
+    P.compute_eta(0, D)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    # ---- device-resident steps
+    for _ in range(max(args.warmup, 3)):
+        P.eval_objective_grad(0, D, G)
+    clocks = Clocks(local)
+    barrier()
+    clocks.start()
+    P.profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        P.eval_objective_grad(0, D, G)
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    kern_ms, kern_n = P.profile_read()
+    P.profile_enable(False)
+
+    # ---- end to end through host buffers
+    Dh = D.cpu().pin_memory()
+    Gh = torch.empty(G.shape, dtype=G.dtype).pin_memory()
+    Dd = torch.empty_like(D)
+    for _ in range(2):
+        Dd.copy_(Dh, non_blocking=True)
+        P.eval_objective_grad(0, Dd, G)
+        Gh.copy_(G, non_blocking=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        Dd.copy_(Dh, non_blocking=True)
+        P.eval_objective_grad(0, Dd, G)
+        Gh.copy_(G, non_blocking=True)
+        stream.synchronize()
+    e1.record(stream)
+    barrier()
+    ms_e2e = e0.elapsed_time(e1)
+    clk = clocks.stop()
+
+    # ---- full solve per pair (all rows: pyramid levels, eta, L-BFGS, prolongation)
+    solve = None
+    if not args.no_solve:
+        out = P.zeros(0)
+        barrier()
+        t0 = time.perf_counter()
+        out, stats = P.solve_full(out)
+        torch.cuda.synchronize()
+        solve = {"seconds_per_pair": time.perf_counter() - t0, "levels": levels,
+                 "evals": int(sum(s["evals"] for s in stats)), "iters": [s["iters"] for s in stats],
+                 "status": [s["status"] for s in stats]}
+
+    # max over ranks
+    t = torch.tensor([ms, ms_e2e], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms, ms_e2e = float(t[0]), float(t[1])
+    if rank != 0:
+        return
+    value = ws * args.steps / (ms / 1e3)
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    kavg = kern_ms / max(kern_n, 1) / 1e3
+    F = flops_per_eval(w, h, d)
+    B = bytes_per_eval(w, h, d)
+    traffic = kernel_traffic(w, h, d)
+    line = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "%s: orthogonal scan pair %dx%d A-scans x %d samples, float32, "
+                               "%d-level pyramid, synthetic retina + vessels + motion" % (args.workload, w, h, d, levels),
+                   "w": w, "h": h, "d": d, "levels": levels, "l2": "inputs larger than L2 (368 MB > 129 MB)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "roofline": {"bound": "alu", "achieved": F / kavg / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": F / kavg / 1e12 / alu_peak, "traffic": traffic,
+                     "kernel": "data_kernel", "kernel_ms": kavg * 1e3,
+                     "flops_per_launch": F, "bytes_per_launch": B,
+                     "hbm_gbs": B / kavg / 1e9, "hbm_peak_gbs": hbm_peak, "hbm_frac": B / kavg / 1e9 / hbm_peak,
+                     "peak_note": "alu peak derived: 152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz; "
+                                  "hbm peak of measured" % sm_max},
+        "e2e": {"value": ws * args.steps / (ms_e2e / 1e3), "unit": "evals/s",
+                "h2d_bytes_per_step": int(Dh.numel() * 8), "d2h_bytes_per_step": int(Gh.numel() * 8)},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk,
+        "solve": solve,
+    }
+    if not args.no_cpu and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(pair, cfg)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/*
+ * octmc — GB300-native (sm_103a) orthogonal-raster OCT/OCTA motion
+ * correction: the joint registration objective, its per-A-scan displacement
+ * gradient, and the multi-resolution L-BFGS solve around it.
+ *
+ * Method: Ploner et al., "Efficient and high accuracy 3-D OCT angiography
+ * motion correction in pathology" (arXiv 2010.06931), Sec. 2.1-2.4.
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ *  - Grid: w x h A-scans of d samples (Sec. 2.1).  0-based indices i (x,
+ *    fast axis of the X-fast scan), j (y), k (depth), in pixels of the level.
+ *  - Volumes: float32 [h][w][d], depth contiguous, both scans in the common
+ *    frame (the Y-fast scan is NOT stored in its acquisition order).
+ *  - En-face angiography A^V (Eq. 6): float32 [h][w].
+ *  - Validity v^X: float32 [h] (one value per X-fast B-scan = row j);
+ *    v^Y: float32 [w] (one value per Y-fast B-scan = column i)  (Sec. 2.2).
+ *  - Sampling-time maps t^V: float64 [h][w], any monotone unit (they order
+ *    the A-scans for the temporal regulariser and weight flyback steps).
+ *  - Displacements D and gradients: float64 [2][3][h_l][w_l] =
+ *    [volume X,Y][component dx,dy,dz][j][i] of level l (Sec. 2.1: one
+ *    3-D displacement per A-scan and volume).
+ *  - Objective (Eq. 1 with Eq. 9): f = eta*S^str + S^ang/eta + alpha*R + M.
+ *  - Every call is ordered on the problem's CUDA stream; "device" pointers
+ *    are CUDA global memory the caller owns; "host" pointers are ordinary
+ *    memory.  Calls on one problem are not thread-safe.
+ *  - Return codes: 0 OK, 1 NOT_CONVERGED (soft: results are valid), negative
+ *    = hard error (see OCTMC_ERR_*); no exception crosses this boundary.
+ */
+#ifndef OCTMC_H
+#define OCTMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OCTMC_OK 0
+#define OCTMC_NOT_CONVERGED 1
+#define OCTMC_ERR_INVALID_ARG (-1)
+#define OCTMC_ERR_OOM (-2)
+#define OCTMC_ERR_CUDA (-3)
+#define OCTMC_ERR_NONFINITE (-4)
+#define OCTMC_ERR_TIMEOUT (-5)
+#define OCTMC_ERR_UNSUPPORTED (-6)
+
+typedef enum { OCTMC_F32 = 0, OCTMC_BF16 = 1, OCTMC_F16 = 2 } octmc_dtype;
+typedef enum { OCTMC_LOSS_PSEUDO_HUBER = 0, OCTMC_LOSS_SSD = 1 } octmc_loss;
+
+typedef struct octmc_problem octmc_problem; /* opaque; owns all its device memory */
+
+/* Problem description (Sec. 2.1 inputs plus solver settings). */
+typedef struct {
+    int w, h, d;          /* level-0 grid; each >= 1                                  */
+    int storage;          /* octmc_dtype of the device copies of S^X, S^Y              */
+    const float *sx, *sy; /* [h][w][d] structural volumes (required)                   */
+    const float *ax, *ay; /* [h][w] en-face angiography, or both NULL (delta = 0)      */
+    const float *vx, *vy; /* vx[h], vy[w] validity, or NULL (all B-scans valid)        */
+    const double *tx, *ty;/* [h][w] sampling-time maps (required)                      */
+    int inputs_on_device; /* 1: the pointers above are device memory, 0: host memory   */
+    double alpha;         /* weight of the temporal regulariser R (default 0.1)        */
+    double delta0;        /* default angio weight delta_0, Eq. 8 (default 0.5)         */
+    double eps_h;         /* pseudo-Huber parameter of the data term, Eq. 4 (0.001)    */
+    double eps_r;         /* pseudo-Huber parameter of R (default 0.01 px)             */
+    double mu;            /* weight of M; <= 0 selects 1/(2 w_l h_l) per level          */
+    int loss;             /* octmc_loss                                                */
+    int levels;           /* pyramid levels, >= 1 (factor 2 each, Sec. 2.1)            */
+    int lbfgs_m;          /* L-BFGS history length, 1..32 (default 8)                  */
+    int max_iter;         /* L-BFGS iterations per level                               */
+    int max_ls;           /* objective evaluations per line search                     */
+    double gtol;          /* stop when max|grad| <= gtol                               */
+    double ftol;          /* stop after 3 iterations with relative decrease < ftol     */
+    void *stream;         /* cudaStream_t (NULL = the legacy default stream)           */
+} octmc_desc;
+
+/* Per-level statistics of a solve. */
+typedef struct {
+    int level;            /* pyramid level solved                                      */
+    int iters;            /* accepted L-BFGS iterations                                */
+    int evals;            /* objective + gradient evaluations                          */
+    int status;           /* 0 converged, 1 iteration cap, 2 line search exhausted     */
+    double f;             /* final objective                                           */
+    double eta;           /* eta used on this level (Eq. 10)                           */
+    double seconds;       /* wall time of the level                                    */
+} octmc_stats;
+
+/* Fills a description with the defaults named above (pointers NULL). */
+void octmc_desc_defaults(octmc_desc *desc);
+
+/* Creates a problem: validates the description, copies the inputs to the
+ * device (converting the volumes to `storage` with round-to-nearest-even),
+ * builds the factor-2 pyramid (Sec. 2.1; box mean, odd sizes repeat the
+ * edge sample) and the time-ordered A-scan chains of each level.
+ * The caller's buffers may be freed afterwards.  *out receives the problem.
+ * Errors: INVALID_ARG (NULL required pointer, dims < 1, levels too deep for
+ * the grid, unknown dtype/loss), OOM, CUDA, UNSUPPORTED (no sm_103a device). */
+int octmc_create_problem(const octmc_desc *desc, octmc_problem **out);
+
+/* Releases every device and host resource of the problem (NULL is a no-op). */
+void octmc_destroy_problem(octmc_problem *p);
+
+/* Grid size (w, h, d) of pyramid level `level` (0 = full resolution). */
+int octmc_level_shape(const octmc_problem *p, int level, int *w, int *h, int *d);
+
+/* Sets eta (Eq. 9) used by later evaluations of `level` (eta > 0, finite). */
+int octmc_set_eta(octmc_problem *p, int level, double eta);
+
+/* Eq. 10: eta = sqrt(S^ang_0.5(D0) / S^str_0.5(D0)) at the device field
+ * disp0 (always with delta_0 = 0.5).  eta = 1 without angiography or when
+ * either sum is zero or not finite.  Stores it for the level and returns it
+ * in *eta_out (host). */
+int octmc_compute_eta(octmc_problem *p, int level, const double *disp0_dev, double *eta_out);
+
+/* Objective and gradient at the device field disp_dev of `level` (Eq. 1-10
+ * with the regulariser and mean-term readings documented in the design
+ * notes).  *f_host receives f (host, may be NULL); grad_dev (device, may be
+ * NULL) receives df/dD in the displacement layout.  Uses the level's stored
+ * eta (1 until set or computed).  Errors: INVALID_ARG, CUDA, NONFINITE
+ * (f is NaN/Inf: the gradient is still written). */
+int octmc_eval_objective_grad(octmc_problem *p, int level, const double *disp_dev, double *f_host,
+                              double *grad_dev);
+
+/* As octmc_eval_objective_grad, and terms_host[6] receives
+ * [S^str, S^ang, R, M, f, eta] (Eq. 5, Eq. 6, R, M, f, eta). */
+int octmc_eval_terms(octmc_problem *p, int level, const double *disp_dev, double *terms_host,
+                     double *grad_dev);
+
+/* L-BFGS solve of one level (Sec. 2.1) from the device field disp_inout
+ * (overwritten with the result).  eta is first computed from the initial
+ * field (Eq. 10).  Returns OK, NOT_CONVERGED (iteration cap) or an error;
+ * st (host, may be NULL) receives the statistics. */
+int octmc_solve_level(octmc_problem *p, int level, double *disp_inout_dev, octmc_stats *st);
+
+/* Full coarse-to-fine solve (Sec. 2.1): zero displacements at the coarsest
+ * level, solve, prolong (x2 values, centre-aligned bilinear), ... down to
+ * level 0.  disp_out_dev receives the level-0 field; st (host, may be
+ * NULL) receives `levels` entries ordered coarse to fine. */
+int octmc_solve_full(octmc_problem *p, double *disp_out_dev, octmc_stats *st);
+
+/* Prolongs a displacement field of level `level` (device) to level-1
+ * (device): every component doubled, bilinear at (i - 1/2)/2 on the coarse
+ * grid with clamped coordinates. */
+int octmc_prolong(octmc_problem *p, int level, const double *coarse_dev, double *fine_dev);
+
+/* Copies pyramid data of `level` to device buffers (any may be NULL):
+ * sx/sy as float32 [h][w][d], ax/ay [h][w], vx[h], vy[w]. */
+int octmc_level_data(const octmc_problem *p, int level, float *sx, float *sy, float *ax, float *ay,
+                     float *vx, float *vy);
+
+/* ---------------------------------------------------------------------
+ * Stand-alone L-BFGS (Sec. 2.1) over n float64 device values: the compact
+ * representation of the inverse Hessian with gamma = s'y / y'y of the latest
+ * pair; pairs with s'y <= 1e-12 y'y are rejected.
+ * --------------------------------------------------------------------- */
+typedef struct octmc_lbfgs octmc_lbfgs;
+
+int octmc_lbfgs_create(int64_t n, int m, void *stream, octmc_lbfgs **out);
+void octmc_lbfgs_destroy(octmc_lbfgs *h);
+/* Appends the pair (s, y) (device).  Returns 0 if stored, 1 if rejected. */
+int octmc_lbfgs_push(octmc_lbfgs *h, const double *s_dev, const double *y_dev);
+/* dir_dev = -H g_dev for the stored pairs; *gtd_host (may be NULL) = g'dir. */
+int octmc_lbfgs_direction(octmc_lbfgs *h, const double *g_dev, double *dir_dev, double *gtd_host);
+/* Drops every stored pair. */
+int octmc_lbfgs_reset(octmc_lbfgs *h);
+
+/* ---------------------------------------------------------------------
+ * Kernel timing: when enabled, every evaluation records CUDA events on the
+ * problem's stream around the data-term kernel (resampling, loss and
+ * per-A-scan gradient) and adds the elapsed time once the evaluation has
+ * synchronised.  Enabling resets the totals.
+ * --------------------------------------------------------------------- */
+int octmc_profile_enable(octmc_problem *p, int enable);
+/* Total milliseconds and number of timed data-term launches so far. */
+int octmc_profile_read(octmc_problem *p, double *total_ms, long long *launches);
+
+/* Human-readable name of a return code. */
+const char *octmc_status_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OCTMC_H */

@@ -1,0 +1,228 @@
+"""GB300-native orthogonal-raster OCT/OCTA motion correction (Ploner et al.,
+arXiv 2010.06931): the joint registration objective, its per-A-scan
+displacement gradient and the multi-resolution L-BFGS solve.
+
+Thin Python binding of the C ABI in ``include/octmc.h``: every method below
+marshals arguments and calls the function of the same name (``octmc_`` +
+name); all arithmetic runs in the CUDA kernels of ``liboctmc.so``.  PyTorch
+provides device memory and the stream only.  There is no CPU fallback: the
+calls raise if the library is not built or no sm_103a GPU is present.
+
+Layouts (see the header): volumes float32 ``[h][w][d]``, en-face images
+``[h][w]``, validity ``vx[h]``, ``vy[w]``, time maps float64 ``[h][w]``,
+displacements and gradients float64 ``[2][3][h][w]`` on the GPU.
+"""
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _native as N
+from ._native import BF16, F16, F32, LOSS_PSEUDO_HUBER, LOSS_SSD, OctmcError  # noqa: F401
+
+__all__ = ["Problem", "Lbfgs", "create_problem", "OctmcError", "F32", "BF16", "F16",
+           "LOSS_PSEUDO_HUBER", "LOSS_SSD", "library_path"]
+
+
+def library_path():
+    return N.LIB_PATH
+
+
+def _stream_ptr():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _as_tensor(a, dtype, device):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        a = torch.from_numpy(np.ascontiguousarray(a))
+    return a.to(device=device, dtype=dtype).contiguous()
+
+
+def _check_disp(t, shape):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("displacement buffers must be contiguous float64 CUDA tensors")
+    if tuple(t.shape) != shape and t.numel() < int(np.prod(shape)):
+        raise ValueError("displacement buffer of shape %s, need %s" % (tuple(t.shape), shape))
+
+
+class Problem:
+    """One orthogonal scan pair on the GPU (``octmc_problem``).
+
+    Inputs may be numpy arrays or torch tensors (host or CUDA); if all the
+    given inputs are CUDA tensors they are read on the device, otherwise from
+    host memory.  Keyword arguments are the fields of ``octmc_desc``.
+    """
+
+    def __init__(self, sx, sy, tx, ty, ax=None, ay=None, vx=None, vy=None, *, storage=F32,
+                 alpha=0.1, delta0=0.5, eps_h=1e-3, eps_r=1e-2, mu=0.0, loss=LOSS_PSEUDO_HUBER,
+                 levels=1, lbfgs_m=8, max_iter=200, max_ls=20, gtol=1e-6, ftol=1e-9):
+        L = N.lib()
+        arrays = [sx, sy, tx, ty, ax, ay, vx, vy]
+        on_dev = all(isinstance(a, torch.Tensor) and a.is_cuda for a in arrays if a is not None)
+        dev = torch.device("cuda") if on_dev else torch.device("cpu")
+        f32 = lambda a: _as_tensor(a, torch.float32, dev)
+        f64 = lambda a: _as_tensor(a, torch.float64, dev)
+        self._keep = dict(sx=f32(sx), sy=f32(sy), tx=f64(tx), ty=f64(ty), ax=f32(ax), ay=f32(ay),
+                          vx=f32(vx), vy=f32(vy))
+        k = self._keep
+        h, w, d = k["sx"].shape
+        desc = N.Desc()
+        L.octmc_desc_defaults(C.byref(desc))
+        desc.w, desc.h, desc.d, desc.storage = w, h, d, storage
+        for name in ("sx", "sy", "ax", "ay", "vx", "vy", "tx", "ty"):
+            setattr(desc, name, None if k[name] is None else k[name].data_ptr())
+        desc.inputs_on_device = 1 if on_dev else 0
+        desc.alpha, desc.delta0, desc.eps_h, desc.eps_r, desc.mu = alpha, delta0, eps_h, eps_r, mu
+        desc.loss, desc.levels, desc.lbfgs_m = loss, levels, lbfgs_m
+        desc.max_iter, desc.max_ls, desc.gtol, desc.ftol = max_iter, max_ls, gtol, ftol
+        desc.stream = _stream_ptr().value
+        self.levels = levels
+        self._h = C.c_void_p()
+        N.check(L.octmc_create_problem(C.byref(desc), C.byref(self._h)), "octmc_create_problem")
+        self._keep = None  # the library copied the inputs
+
+    # -- lifetime
+    def destroy_problem(self):
+        if self._h:
+            N.lib().octmc_destroy_problem(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy_problem()
+        except Exception:
+            pass
+
+    # -- queries
+    def level_shape(self, level=0):
+        w, h, d = C.c_int(), C.c_int(), C.c_int()
+        N.check(N.lib().octmc_level_shape(self._h, level, C.byref(w), C.byref(h), C.byref(d)),
+                "octmc_level_shape")
+        return w.value, h.value, d.value
+
+    def disp_shape(self, level=0):
+        w, h, _ = self.level_shape(level)
+        return (2, 3, h, w)
+
+    def zeros(self, level=0):
+        return torch.zeros(self.disp_shape(level), dtype=torch.float64, device="cuda")
+
+    # -- eta (Eq. 9-10)
+    def set_eta(self, level, eta):
+        N.check(N.lib().octmc_set_eta(self._h, level, float(eta)), "octmc_set_eta")
+
+    def compute_eta(self, level, disp0):
+        _check_disp(disp0, self.disp_shape(level))
+        e = C.c_double()
+        N.check(N.lib().octmc_compute_eta(self._h, level, _ptr(disp0), C.byref(e)), "octmc_compute_eta")
+        return e.value
+
+    # -- objective (Eq. 1-10)
+    def eval_objective_grad(self, level, disp, grad=None):
+        """f (float) and, if ``grad`` is a tensor, the gradient written into it."""
+        _check_disp(disp, self.disp_shape(level))
+        if grad is not None:
+            _check_disp(grad, self.disp_shape(level))
+        f = C.c_double()
+        N.check(N.lib().octmc_eval_objective_grad(self._h, level, _ptr(disp), C.byref(f), _ptr(grad)),
+                "octmc_eval_objective_grad")
+        return f.value
+
+    def eval_terms(self, level, disp, grad=None):
+        """[S^str, S^ang, R, M, f, eta] as a numpy array; optional gradient as above."""
+        _check_disp(disp, self.disp_shape(level))
+        if grad is not None:
+            _check_disp(grad, self.disp_shape(level))
+        t = (C.c_double * 6)()
+        N.check(N.lib().octmc_eval_terms(self._h, level, _ptr(disp), t, _ptr(grad)), "octmc_eval_terms")
+        return np.array(t[:])
+
+    # -- solves (Sec. 2.1)
+    def solve_level(self, level, disp):
+        """In-place L-BFGS solve of ``disp``; returns the statistics dict."""
+        _check_disp(disp, self.disp_shape(level))
+        st = N.Stats()
+        rc = N.check(N.lib().octmc_solve_level(self._h, level, _ptr(disp), C.byref(st)), "octmc_solve_level")
+        out = st.as_dict()
+        out["rc"] = rc
+        return out
+
+    def solve_full(self, out=None):
+        """Coarse-to-fine solve from zero; returns (level-0 field, per-level stats)."""
+        if out is None:
+            out = self.zeros(0)
+        _check_disp(out, self.disp_shape(0))
+        st = (N.Stats * self.levels)()
+        rc = N.check(N.lib().octmc_solve_full(self._h, _ptr(out), st), "octmc_solve_full")
+        stats = [s.as_dict() for s in st]
+        for s in stats:
+            s["rc"] = rc
+        return out, stats
+
+    def prolong(self, level, coarse):
+        _check_disp(coarse, self.disp_shape(level))
+        fine = self.zeros(level - 1)
+        N.check(N.lib().octmc_prolong(self._h, level, _ptr(coarse), _ptr(fine)), "octmc_prolong")
+        return fine
+
+    def level_data(self, level=0):
+        w, h, d = self.level_shape(level)
+        out = {k: torch.empty(s, dtype=torch.float32, device="cuda") for k, s in
+               (("sx", (h, w, d)), ("sy", (h, w, d)), ("ax", (h, w)), ("ay", (h, w)), ("vx", (h,)), ("vy", (w,)))}
+        N.check(N.lib().octmc_level_data(self._h, level, *[_ptr(out[k]) for k in ("sx", "sy", "ax", "ay", "vx", "vy")]),
+                "octmc_level_data")
+        return out
+
+
+    # -- kernel timing
+    def profile_enable(self, enable=True):
+        N.check(N.lib().octmc_profile_enable(self._h, 1 if enable else 0), "octmc_profile_enable")
+
+    def profile_read(self):
+        """(total ms, launches) of the data-term kernel since profiling was enabled."""
+        ms, n = C.c_double(), C.c_longlong()
+        N.check(N.lib().octmc_profile_read(self._h, C.byref(ms), C.byref(n)), "octmc_profile_read")
+        return ms.value, n.value
+
+
+def create_problem(*args, **kw):
+    """``octmc_create_problem``: see :class:`Problem`."""
+    return Problem(*args, **kw)
+
+
+class Lbfgs:
+    """Stand-alone on-device L-BFGS direction (``octmc_lbfgs_*``) over n float64 values."""
+
+    def __init__(self, n, m=8):
+        self.n = int(n)
+        self._h = C.c_void_p()
+        N.check(N.lib().octmc_lbfgs_create(self.n, int(m), _stream_ptr(), C.byref(self._h)), "octmc_lbfgs_create")
+
+    def push(self, s, y):
+        return N.check(N.lib().octmc_lbfgs_push(self._h, _ptr(s), _ptr(y)), "octmc_lbfgs_push")
+
+    def direction(self, g):
+        out = torch.empty_like(g)
+        gtd = C.c_double()
+        N.check(N.lib().octmc_lbfgs_direction(self._h, _ptr(g), _ptr(out), C.byref(gtd)), "octmc_lbfgs_direction")
+        return out, gtd.value
+
+    def reset(self):
+        N.check(N.lib().octmc_lbfgs_reset(self._h), "octmc_lbfgs_reset")
+
+    def destroy(self):
+        if self._h:
+            N.lib().octmc_lbfgs_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

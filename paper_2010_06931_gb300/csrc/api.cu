@@ -1,0 +1,899 @@
+// Host side of liboctmc: the problem object (device pyramid and chains), one
+// objective evaluation, eta, the on-device L-BFGS and the level / full
+// solves, behind the C ABI declared in include/octmc.h.
+//
+// All vectors of the optimiser (displacements, gradients, directions, the
+// L-BFGS history) live in device memory; the host only reads the few
+// scalars the line search and the compact L-BFGS algebra need (f, grad .
+// dir, and 4m+5 dot products per iteration).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace octmc;
+
+namespace {
+
+struct CudaFail {
+  int code;
+};
+
+#define CK(call)                                                       \
+  do {                                                                 \
+    cudaError_t e_ = (call);                                           \
+    if (e_ != cudaSuccess) {                                           \
+      throw CudaFail{e_ == cudaErrorMemoryAllocation ? OCTMC_ERR_OOM   \
+                                                     : OCTMC_ERR_CUDA}; \
+    }                                                                  \
+  } while (0)
+
+template <typename T>
+T* dalloc(size_t count) {
+  void* p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw CudaFail{e == cudaErrorMemoryAllocation ? OCTMC_ERR_OOM : OCTMC_ERR_CUDA};
+  }
+  return static_cast<T*>(p);
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+int half_up(int n) { return (n + 1) / 2; }
+int pad4(int d) { return (d + 3) & ~3; }
+
+// Time-ordered chain of the A-scans of one volume: prev/next neighbour in
+// acquisition order and the weight dt_min / dt of each pair (ties weigh 1).
+void build_chain(const std::vector<double>& t, std::vector<int>& prev, std::vector<int>& next,
+                 std::vector<double>& wprev, std::vector<double>& wnext) {
+  const int n = (int)t.size();
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return t[a] < t[b] || (t[a] == t[b] && a < b); });
+  double dtmin = std::numeric_limits<double>::infinity();
+  for (int m = 0; m + 1 < n; m++) {
+    const double dt = t[order[m + 1]] - t[order[m]];
+    if (dt > 0 && dt < dtmin) dtmin = dt;
+  }
+  prev.assign(n, -1);
+  next.assign(n, -1);
+  wprev.assign(n, 0.0);
+  wnext.assign(n, 0.0);
+  for (int m = 0; m + 1 < n; m++) {
+    const int a = order[m], b = order[m + 1];
+    const double dt = t[b] - t[a];
+    const double om = std::isinf(dtmin) ? 1.0 : dtmin / std::max(dt, dtmin);
+    next[a] = b;
+    wnext[a] = om;
+    prev[b] = a;
+    wprev[b] = om;
+  }
+}
+
+std::vector<double> time_down(const std::vector<double>& t, int w, int h) {
+  const int w2 = half_up(w), h2 = half_up(h);
+  std::vector<double> o((size_t)w2 * h2);
+  for (int j = 0; j < h2; j++)
+    for (int i = 0; i < w2; i++) {
+      const int i1 = std::min(2 * i + 1, w - 1), j1 = std::min(2 * j + 1, h - 1);
+      o[(size_t)j * w2 + i] = (t[(size_t)2 * j * w + 2 * i] + t[(size_t)2 * j * w + i1] +
+                               t[(size_t)j1 * w + 2 * i] + t[(size_t)j1 * w + i1]) /
+                              4.0;
+    }
+  return o;
+}
+
+}  // namespace
+
+// ====================================================================== L-BFGS
+struct octmc_lbfgs {
+  int64_t n = 0;
+  int m = 0;
+  cudaStream_t st = nullptr;
+  std::vector<double*> S, Y;  // m + 1 buffers each
+  std::vector<int> order;     // stored pairs, oldest first (buffer ids)
+  int spare = 0;              // buffer receiving the next pair
+  std::vector<double> SY, YY; // (m+1)^2, indexed by buffer ids
+  double* partials = nullptr;
+  unsigned* counter = nullptr;
+  double* dots_dev = nullptr;
+  double* dots_host = nullptr; // pinned, kMaxDots + 1
+  // results of the last prepare(): per stored buffer s.g and y.g, g.g, max|g|
+  std::vector<double> sg, yg;
+  double gg = 0.0, gmax = 0.0;
+
+  ~octmc_lbfgs() {
+    for (double* p : S) dfree(p);
+    for (double* p : Y) dfree(p);
+    dfree(partials);
+    dfree(counter);
+    dfree(dots_dev);
+    if (dots_host) cudaFreeHost(dots_host);
+  }
+
+  void init(int64_t n_, int m_, cudaStream_t s) {
+    n = n_;
+    m = m_;
+    st = s;
+    S.assign(m + 1, nullptr);
+    Y.assign(m + 1, nullptr);
+    for (int b = 0; b <= m; b++) {
+      S[b] = dalloc<double>((size_t)n);
+      Y[b] = dalloc<double>((size_t)n);
+    }
+    SY.assign((size_t)(m + 1) * (m + 1), 0.0);
+    YY.assign((size_t)(m + 1) * (m + 1), 0.0);
+    sg.assign(m + 1, 0.0);
+    yg.assign(m + 1, 0.0);
+    partials = dalloc<double>((size_t)(kMaxDots + 1) * dots_grid_blocks(n));
+    counter = dalloc<unsigned>(1);
+    CK(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
+    dots_dev = dalloc<double>(kMaxDots + 1);
+    CK(cudaMallocHost(&dots_host, sizeof(double) * (kMaxDots + 1)));
+    reset();
+  }
+
+  void reset() {
+    order.clear();
+    spare = 0;
+  }
+  int k() const { return (int)order.size(); }
+  double& sy(int a, int b) { return SY[(size_t)a * (m + 1) + b]; }
+  double& yy(int a, int b) { return YY[(size_t)a * (m + 1) + b]; }
+
+  int free_buffer() const {
+    for (int b = 0; b <= m; b++)
+      if (std::find(order.begin(), order.end(), b) == order.end()) return b;
+    return 0;
+  }
+
+  // One pass over the history: if new_pair, the pair in buffer `spare` is
+  // tested (s'y > 1e-12 y'y) and appended (dropping the oldest when full);
+  // if g != null, s.g and y.g for every stored pair plus g.g and max|g| are
+  // taken for the next direction.  Returns 1 if a new pair was rejected.
+  int prepare(const double* g, bool new_pair) {
+    DotList dl;
+    dl.n = 0;
+    const int nb = spare;
+    auto add = [&](const double* a, const double* b) {
+      dl.a[dl.n] = a;
+      dl.b[dl.n] = b;
+      dl.n++;
+    };
+    if (new_pair) {
+      add(S[nb], Y[nb]);
+      add(Y[nb], Y[nb]);
+      for (int b : order) {
+        add(S[b], Y[nb]);
+        add(Y[b], Y[nb]);
+      }
+    }
+    const int first_g = dl.n;
+    std::vector<int> cand = order;
+    if (new_pair) cand.push_back(nb);
+    if (g) {
+      for (int b : cand) {
+        add(S[b], g);
+        add(Y[b], g);
+      }
+      add(g, g);
+    }
+    CK(launch_dots(dl, n, g, partials, counter, dots_dev, st));
+    CK(cudaMemcpyAsync(dots_host, dots_dev, sizeof(double) * (kMaxDots + 1), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const double* r = dots_host;
+    int rejected = 0;
+    if (new_pair) {
+      const double s_y = r[0], y_y = r[1];
+      if (s_y > 1e-12 * y_y && std::isfinite(s_y) && std::isfinite(y_y)) {
+        for (size_t t = 0; t < order.size(); t++) {
+          sy(order[t], nb) = r[2 + 2 * t];
+          const double v = r[3 + 2 * t];
+          yy(order[t], nb) = v;
+          yy(nb, order[t]) = v;
+        }
+        sy(nb, nb) = s_y;
+        yy(nb, nb) = y_y;
+        if ((int)order.size() == m) order.erase(order.begin());
+        order.push_back(nb);
+        spare = free_buffer();
+      } else {
+        rejected = 1;
+      }
+    }
+    if (g) {
+      for (size_t t = 0; t < cand.size(); t++) {
+        sg[cand[t]] = r[first_g + 2 * t];
+        yg[cand[t]] = r[first_g + 2 * t + 1];
+      }
+      gg = r[first_g + 2 * cand.size()];
+      gmax = r[kMaxDots];
+    }
+    return rejected;
+  }
+
+  // dir = -H g (compact form of Byrd, Nocedal & Schnabel with H0 = gamma I),
+  // using the s.g / y.g of the last prepare(g).  Returns g . dir; when that
+  // is not negative the history is dropped and dir = -g.
+  double direction(const double* g, double* dir) {
+    const int k = this->k();
+    LinComb lc;
+    double gd;
+    if (k > 0) {
+      const int last = order[k - 1];
+      const double gamma = sy(last, last) / yy(last, last);
+      std::vector<double> a(k), b(k), u(k), wv(k), top(k);
+      for (int i = 0; i < k; i++) {
+        a[i] = sg[order[i]];
+        b[i] = yg[order[i]];
+      }
+      // u = R^{-1} a, R_ij = s_i . y_j (i <= j)
+      for (int i = k - 1; i >= 0; i--) {
+        double s = a[i];
+        for (int j = i + 1; j < k; j++) s -= sy(order[i], order[j]) * u[j];
+        u[i] = s / sy(order[i], order[i]);
+      }
+      // w = (D + gamma Y'Y) u - gamma b
+      for (int i = 0; i < k; i++) {
+        double s = sy(order[i], order[i]) * u[i];
+        for (int j = 0; j < k; j++) s += gamma * yy(order[i], order[j]) * u[j];
+        wv[i] = s - gamma * b[i];
+      }
+      // top = R^{-T} w
+      for (int i = 0; i < k; i++) {
+        double s = wv[i];
+        for (int j = 0; j < i; j++) s -= sy(order[j], order[i]) * top[j];
+        top[i] = s / sy(order[i], order[i]);
+      }
+      lc.n = 0;
+      lc.v[lc.n] = g;
+      lc.c[lc.n++] = -gamma;
+      gd = -gamma * gg;
+      for (int i = 0; i < k; i++) {
+        lc.v[lc.n] = S[order[i]];
+        lc.c[lc.n++] = -top[i];
+        lc.v[lc.n] = Y[order[i]];
+        lc.c[lc.n++] = gamma * u[i];
+        gd += -top[i] * a[i] + gamma * u[i] * b[i];
+      }
+      if (!(gd < 0.0)) k_reset_steepest(lc, g, gd);
+    } else {
+      k_reset_steepest(lc, g, gd);
+    }
+    CK(launch_lincomb(lc, n, dir, st));
+    return gd;
+  }
+
+  void k_reset_steepest(LinComb& lc, const double* g, double& gd) {
+    reset();
+    lc.n = 1;
+    lc.v[0] = g;
+    lc.c[0] = -1.0;
+    gd = -gg;
+  }
+};
+
+// ====================================================================== problem
+struct Level {
+  LevelDev dev{};
+  double eta = 1.0;
+  double mu = 0.0;
+};
+
+struct octmc_problem {
+  octmc_desc desc{};
+  cudaStream_t st = nullptr;
+  bool have_ang = false;
+  std::vector<Level> lv;
+  // evaluation workspace (sized for level 0)
+  double* str = nullptr;
+  double* ang = nullptr;
+  double* partials = nullptr;
+  unsigned* counters = nullptr;  // [0] msum, [1] reg
+  EvalResult* res = nullptr;
+  EvalResult* res_host = nullptr;  // pinned
+  // solver workspace (level-0 sized, allocated on first solve)
+  double* x = nullptr;
+  double* g = nullptr;
+  double* xt = nullptr;
+  double* gt = nullptr;
+  double* xb = nullptr;
+  double* gb = nullptr;
+  double* dir = nullptr;
+  octmc_lbfgs* opt = nullptr;
+  // optional CUDA-event timing of the data-term kernel (octmc_profile_*)
+  bool profile = false;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double prof_ms = 0.0;
+  long long prof_count = 0;
+  bool prof_pending = false;
+
+  ~octmc_problem() {
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    for (Level& L : lv) {
+      LevelDev& d = L.dev;
+      dfree(d.sx); dfree(d.sy); dfree(d.ax); dfree(d.ay); dfree(d.vx); dfree(d.vy);
+      for (int V = 0; V < 2; V++) {
+        dfree(d.prev[V]); dfree(d.next[V]); dfree(d.wprev[V]); dfree(d.wnext[V]);
+      }
+    }
+    dfree(str); dfree(ang); dfree(partials); dfree(counters); dfree(res);
+    if (res_host) cudaFreeHost(res_host);
+    dfree(x); dfree(g); dfree(xt); dfree(gt); dfree(xb); dfree(gb); dfree(dir);
+    delete opt;
+  }
+
+  int64_t plane(int l) const { return (int64_t)lv[l].dev.w * lv[l].dev.h; }
+};
+
+namespace {
+
+void check_device() {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, dev));
+  if (!(prop.major == 10 && prop.minor == 3)) throw CudaFail{OCTMC_ERR_UNSUPPORTED};
+}
+
+void upload_volume(octmc_problem* P, const float* src, float* dst, int w, int h, int d, int dp) {
+  const cudaMemcpyKind kind = P->desc.inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const int64_t cols = (int64_t)w * h;
+  // rows of d samples into rows of dp; cudaMemcpy2D limits the row count to
+  // what a size_t height takes, so copy in slabs of columns
+  const int64_t slab = 1 << 20;
+  for (int64_t c0 = 0; c0 < cols; c0 += slab) {
+    const int64_t nc = std::min(slab, cols - c0);
+    CK(cudaMemcpy2DAsync(dst + c0 * dp, sizeof(float) * dp, src + c0 * d, sizeof(float) * d,
+                         sizeof(float) * d, (size_t)nc, kind, P->st));
+  }
+  CK(launch_pad_depth(dst, cols, d, dp, P->st));
+}
+
+template <typename T>
+void upload(octmc_problem* P, const T* src, T* dst, size_t count) {
+  const cudaMemcpyKind kind = P->desc.inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpyAsync(dst, src, sizeof(T) * count, kind, P->st));
+}
+
+template <typename T>
+void upload_host(octmc_problem* P, const std::vector<T>& v, T* dst) {
+  CK(cudaMemcpyAsync(dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, P->st));
+}
+
+std::vector<double> fetch_times(octmc_problem* P, const double* t, size_t n) {
+  std::vector<double> out(n);
+  if (P->desc.inputs_on_device) {
+    CK(cudaMemcpyAsync(out.data(), t, sizeof(double) * n, cudaMemcpyDeviceToHost, P->st));
+    CK(cudaStreamSynchronize(P->st));
+  } else {
+    std::memcpy(out.data(), t, sizeof(double) * n);
+  }
+  for (double v : out)
+    if (!std::isfinite(v)) throw CudaFail{OCTMC_ERR_INVALID_ARG};
+  return out;
+}
+
+void create_impl(octmc_problem* P) {
+  const octmc_desc& D = P->desc;
+  check_device();
+  const int L = D.levels;
+  P->lv.resize(L);
+  int w = D.w, h = D.h, d = D.d;
+  std::vector<double> tx = fetch_times(P, D.tx, (size_t)w * h), ty = fetch_times(P, D.ty, (size_t)w * h);
+  for (int l = 0; l < L; l++) {
+    LevelDev& X = P->lv[l].dev;
+    X.w = w; X.h = h; X.d = d; X.dp = pad4(d);
+    const int64_t cols = (int64_t)w * h;
+    X.sx = dalloc<float>((size_t)cols * X.dp);
+    X.sy = dalloc<float>((size_t)cols * X.dp);
+    if (P->have_ang) {
+      X.ax = dalloc<float>((size_t)cols);
+      X.ay = dalloc<float>((size_t)cols);
+    }
+    if (D.vx) X.vx = dalloc<float>((size_t)h);
+    if (D.vy) X.vy = dalloc<float>((size_t)w);
+    if (l == 0) {
+      upload_volume(P, D.sx, X.sx, w, h, d, X.dp);
+      upload_volume(P, D.sy, X.sy, w, h, d, X.dp);
+      if (P->have_ang) {
+        upload(P, D.ax, X.ax, (size_t)cols);
+        upload(P, D.ay, X.ay, (size_t)cols);
+      }
+      if (D.vx) upload(P, D.vx, X.vx, (size_t)h);
+      if (D.vy) upload(P, D.vy, X.vy, (size_t)w);
+    } else {
+      const LevelDev& F = P->lv[l - 1].dev;
+      CK(launch_pyr_volume(F.sx, F.w, F.h, F.d, F.dp, X.sx, w, h, d, X.dp, P->st));
+      CK(launch_pyr_volume(F.sy, F.w, F.h, F.d, F.dp, X.sy, w, h, d, X.dp, P->st));
+      if (P->have_ang) {
+        CK(launch_pyr_image(F.ax, F.w, F.h, X.ax, P->st));
+        CK(launch_pyr_image(F.ay, F.w, F.h, X.ay, P->st));
+      }
+      if (X.vx) CK(launch_pyr_line(F.vx, F.h, X.vx, P->st));
+      if (X.vy) CK(launch_pyr_line(F.vy, F.w, X.vy, P->st));
+      tx = time_down(tx, F.w, F.h);
+      ty = time_down(ty, F.w, F.h);
+    }
+    for (int V = 0; V < 2; V++) {
+      std::vector<int> pv, nx;
+      std::vector<double> wp, wn;
+      build_chain(V == 0 ? tx : ty, pv, nx, wp, wn);
+      X.prev[V] = dalloc<int>((size_t)cols);
+      X.next[V] = dalloc<int>((size_t)cols);
+      X.wprev[V] = dalloc<double>((size_t)cols);
+      X.wnext[V] = dalloc<double>((size_t)cols);
+      upload_host(P, pv, X.prev[V]);
+      upload_host(P, nx, X.next[V]);
+      upload_host(P, wp, X.wprev[V]);
+      upload_host(P, wn, X.wnext[V]);
+      CK(cudaStreamSynchronize(P->st));  // host vectors go out of scope
+    }
+    P->lv[l].mu = D.mu > 0 ? D.mu : 1.0 / (2.0 * (double)w * (double)h);
+    w = half_up(w);
+    h = half_up(h);
+    d = half_up(d);
+  }
+  const int64_t n0 = P->plane(0);
+  P->str = dalloc<double>((size_t)n0);
+  P->ang = dalloc<double>((size_t)n0);
+  P->partials = dalloc<double>((size_t)8 * std::max(reg_grid_blocks(n0), msum_grid_blocks()));
+  P->counters = dalloc<unsigned>(2);
+  CK(cudaMemsetAsync(P->counters, 0, 2 * sizeof(unsigned), P->st));
+  P->res = dalloc<EvalResult>(1);
+  CK(cudaMallocHost(&P->res_host, sizeof(EvalResult)));
+  CK(cudaStreamSynchronize(P->st));
+}
+
+void collect_profile(octmc_problem* P) {
+  if (!P->prof_pending) return;
+  float ms = 0.f;
+  CK(cudaEventSynchronize(P->ev1));
+  CK(cudaEventElapsedTime(&ms, P->ev0, P->ev1));
+  P->prof_ms += ms;
+  P->prof_count++;
+  P->prof_pending = false;
+}
+
+// One objective (+ gradient) evaluation.  Enqueues msum -> data -> reg and,
+// if sync, waits and copies the EvalResult to the host.
+void eval_impl(octmc_problem* P, int l, const double* disp, double* grad, const double* dir, double eta,
+               double delta0, bool sync) {
+  const Level& Lv = P->lv[l];
+  const int64_t n = P->plane(l);
+  CK(launch_msum(disp, n, P->res, P->partials, P->counters + 0, P->st));
+  DataArgs A;
+  A.L = Lv.dev;
+  A.disp = disp;
+  A.str_out = P->str;
+  A.ang_out = P->ang;
+  A.grad = grad;
+  A.eta = eta;
+  A.delta0 = P->have_ang ? delta0 : 0.0;
+  A.eps_h = (float)P->desc.eps_h;
+  A.loss = P->desc.loss;
+  if (P->profile) CK(cudaEventRecord(P->ev0, P->st));
+  CK(launch_data(A, P->st));
+  if (P->profile) {
+    CK(cudaEventRecord(P->ev1, P->st));
+    P->prof_pending = true;
+  }
+  RegArgs R;
+  R.L = Lv.dev;
+  R.disp = disp;
+  R.grad = grad;
+  R.dir = dir;
+  R.str_in = P->str;
+  R.ang_in = P->ang;
+  R.alpha = P->desc.alpha;
+  R.eps_r = P->desc.eps_r;
+  R.mu = Lv.mu;
+  R.eta = eta;
+  R.result = P->res;
+  R.partials = P->partials;
+  R.counter = P->counters + 1;
+  CK(launch_reg(R, P->st));
+  if (sync) {
+    CK(cudaMemcpyAsync(P->res_host, P->res, sizeof(EvalResult), cudaMemcpyDeviceToHost, P->st));
+    CK(cudaStreamSynchronize(P->st));
+  }
+  if (P->profile && sync) collect_profile(P);
+}
+
+double eta_impl(octmc_problem* P, int l, const double* disp0) {
+  if (!P->have_ang) return 1.0;
+  eval_impl(P, l, disp0, nullptr, nullptr, 1.0, 0.5, true);
+  const double s = P->res_host->terms[0], a = P->res_host->terms[1];
+  const double e = std::sqrt(a / s);
+  if (!(s > 0) || !(a > 0) || !std::isfinite(e)) return 1.0;
+  return e;
+}
+
+void ensure_solver(octmc_problem* P) {
+  if (P->x) return;
+  const size_t n = (size_t)6 * P->plane(0);
+  P->x = dalloc<double>(n);
+  P->g = dalloc<double>(n);
+  P->xt = dalloc<double>(n);
+  P->gt = dalloc<double>(n);
+  P->xb = dalloc<double>(n);
+  P->gb = dalloc<double>(n);
+  P->dir = dalloc<double>(n);
+  P->opt = new octmc_lbfgs();
+  P->opt->init((int64_t)n, P->desc.lbfgs_m, P->st);
+}
+
+// The level solve: same algorithm and constants as the CPU reference solver
+// (weak-Wolfe bisection line search, c1 = 1e-4, c2 = 0.9; a0 = 1/||g|| on an
+// empty history; best Armijo point, else one retry from -g, else stop).
+int solve_impl(octmc_problem* P, int l, double* disp_inout, octmc_stats* st) {
+  const auto t0 = std::chrono::steady_clock::now();
+  ensure_solver(P);
+  const int64_t n = 6 * P->plane(l);
+  octmc_lbfgs* O = P->opt;
+  O->n = n;  // history buffers are level-0 sized; use the first n entries
+  O->reset();
+  const double eta = eta_impl(P, l, disp_inout);
+  P->lv[l].eta = eta;
+  const double delta0 = P->desc.delta0;
+  double *x = P->x, *g = P->g, *xt = P->xt, *gt = P->gt, *xb = P->xb, *gb = P->gb, *dir = P->dir;
+  CK(cudaMemcpyAsync(x, disp_inout, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->st));
+  eval_impl(P, l, x, g, nullptr, eta, delta0, true);
+  double f = P->res_host->terms[4];
+  int evals = 1, iters = 0, status = 1, small = 0, retried = 0;
+  O->prepare(g, false);
+  while (iters < P->desc.max_iter) {
+    if (O->gmax <= P->desc.gtol) {
+      status = 0;
+      break;
+    }
+    const int k = O->k();
+    const double dg0 = O->direction(g, dir);
+    double a = (O->k() == 0) ? 1.0 / std::sqrt(O->gg) : 1.0;
+    (void)k;
+    double lo = 0.0, hi = std::numeric_limits<double>::infinity(), ft = 0.0, fb = 0.0;
+    bool accepted = false, have_lo = false;
+    for (int ls = 0; ls < P->desc.max_ls; ls++) {
+      CK(launch_axpy(x, a, dir, xt, n, P->st));
+      eval_impl(P, l, xt, gt, dir, eta, delta0, true);
+      evals++;
+      ft = P->res_host->terms[4];
+      const double dgt = P->res_host->gdir;
+      if (!(ft <= f + 1e-4 * a * dg0)) {
+        hi = a;
+        a = 0.5 * (lo + hi);
+      } else if (dgt < 0.9 * dg0) {
+        lo = a;
+        have_lo = true;
+        fb = ft;
+        std::swap(xb, xt);
+        std::swap(gb, gt);
+        a = std::isinf(hi) ? 2.0 * a : 0.5 * (lo + hi);
+      } else {
+        accepted = true;
+        break;
+      }
+    }
+    if (!accepted) {
+      if (have_lo) {
+        std::swap(xt, xb);
+        std::swap(gt, gb);
+        ft = fb;
+      } else if (O->k() > 0 && !retried) {
+        O->reset();
+        retried = 1;
+        O->prepare(g, false);
+        continue;
+      } else {
+        status = 2;
+        break;
+      }
+    }
+    retried = 0;
+    CK(launch_sub2(xt, x, gt, g, O->S[O->spare], O->Y[O->spare], n, P->st));
+    const double rel = (f - ft) / std::max(std::max(std::fabs(f), std::fabs(ft)), 1.0);
+    std::swap(x, xt);
+    std::swap(g, gt);
+    f = ft;
+    iters++;
+    O->prepare(g, true);
+    small = (rel < P->desc.ftol) ? small + 1 : 0;
+    if (small >= 3) {
+      status = 0;
+      break;
+    }
+  }
+  CK(cudaMemcpyAsync(disp_inout, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->st));
+  CK(cudaStreamSynchronize(P->st));
+  if (st) {
+    st->level = l;
+    st->iters = iters;
+    st->evals = evals;
+    st->status = status;
+    st->f = f;
+    st->eta = eta;
+    st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (!std::isfinite(f)) return OCTMC_ERR_NONFINITE;
+  return status == 1 ? OCTMC_NOT_CONVERGED : OCTMC_OK;
+}
+
+template <typename F>
+int guarded(F&& f) {
+  try {
+    return f();
+  } catch (const CudaFail& e) {
+    cudaGetLastError();
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    return OCTMC_ERR_OOM;
+  } catch (...) {
+    return OCTMC_ERR_CUDA;
+  }
+}
+
+bool valid_level(const octmc_problem* p, int level) { return p && level >= 0 && level < (int)p->lv.size(); }
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+void octmc_desc_defaults(octmc_desc* d) {
+  if (!d) return;
+  std::memset(d, 0, sizeof(*d));
+  d->storage = OCTMC_F32;
+  d->alpha = 0.1;
+  d->delta0 = 0.5;
+  d->eps_h = 1e-3;
+  d->eps_r = 1e-2;
+  d->mu = 0.0;
+  d->loss = OCTMC_LOSS_PSEUDO_HUBER;
+  d->levels = 1;
+  d->lbfgs_m = 8;
+  d->max_iter = 200;
+  d->max_ls = 20;
+  d->gtol = 1e-6;
+  d->ftol = 1e-9;
+}
+
+int octmc_create_problem(const octmc_desc* desc, octmc_problem** out) {
+  if (!desc || !out) return OCTMC_ERR_INVALID_ARG;
+  *out = nullptr;
+  const octmc_desc& D = *desc;
+  if (D.w < 1 || D.h < 1 || D.d < 1 || !D.sx || !D.sy || !D.tx || !D.ty) return OCTMC_ERR_INVALID_ARG;
+  if ((D.ax == nullptr) != (D.ay == nullptr)) return OCTMC_ERR_INVALID_ARG;
+  if (D.levels < 1 || D.levels > 16 || D.lbfgs_m < 1 || D.lbfgs_m > 32 || D.max_ls < 1 || D.max_iter < 0)
+    return OCTMC_ERR_INVALID_ARG;
+  if (D.loss != OCTMC_LOSS_PSEUDO_HUBER && D.loss != OCTMC_LOSS_SSD) return OCTMC_ERR_INVALID_ARG;
+  if (!(D.eps_h > 0) || !(D.eps_r > 0) || !(D.alpha >= 0) || !(D.delta0 >= 0)) return OCTMC_ERR_INVALID_ARG;
+  if ((int64_t)D.w * D.h * pad4(D.d) / 4 >= (int64_t)1 << 32) return OCTMC_ERR_INVALID_ARG;
+  if (D.storage != OCTMC_F32) {
+    if (D.storage == OCTMC_BF16 || D.storage == OCTMC_F16) return OCTMC_ERR_UNSUPPORTED;
+    return OCTMC_ERR_INVALID_ARG;
+  }
+  octmc_problem* P = new (std::nothrow) octmc_problem();
+  if (!P) return OCTMC_ERR_OOM;
+  P->desc = D;
+  P->st = (cudaStream_t)D.stream;
+  P->have_ang = (D.ax != nullptr);
+  const int rc = guarded([&] {
+    create_impl(P);
+    return OCTMC_OK;
+  });
+  if (rc != OCTMC_OK) {
+    delete P;
+    return rc;
+  }
+  *out = P;
+  return OCTMC_OK;
+}
+
+void octmc_destroy_problem(octmc_problem* p) {
+  if (!p) return;
+  if (p->st) cudaStreamSynchronize(p->st);
+  else cudaDeviceSynchronize();
+  delete p;
+}
+
+int octmc_level_shape(const octmc_problem* p, int level, int* w, int* h, int* d) {
+  if (!valid_level(p, level)) return OCTMC_ERR_INVALID_ARG;
+  const LevelDev& L = p->lv[level].dev;
+  if (w) *w = L.w;
+  if (h) *h = L.h;
+  if (d) *d = L.d;
+  return OCTMC_OK;
+}
+
+int octmc_set_eta(octmc_problem* p, int level, double eta) {
+  if (!valid_level(p, level) || !(eta > 0) || !std::isfinite(eta)) return OCTMC_ERR_INVALID_ARG;
+  p->lv[level].eta = eta;
+  return OCTMC_OK;
+}
+
+int octmc_compute_eta(octmc_problem* p, int level, const double* disp0, double* eta_out) {
+  if (!valid_level(p, level) || !disp0) return OCTMC_ERR_INVALID_ARG;
+  return guarded([&] {
+    const double e = eta_impl(p, level, disp0);
+    p->lv[level].eta = e;
+    if (eta_out) *eta_out = e;
+    return OCTMC_OK;
+  });
+}
+
+int octmc_eval_terms(octmc_problem* p, int level, const double* disp, double* terms, double* grad) {
+  if (!valid_level(p, level) || !disp) return OCTMC_ERR_INVALID_ARG;
+  return guarded([&] {
+    eval_impl(p, level, disp, grad, nullptr, p->lv[level].eta, p->desc.delta0, true);
+    if (terms) std::memcpy(terms, p->res_host->terms, sizeof(double) * 6);
+    return std::isfinite(p->res_host->terms[4]) ? OCTMC_OK : OCTMC_ERR_NONFINITE;
+  });
+}
+
+int octmc_eval_objective_grad(octmc_problem* p, int level, const double* disp, double* f, double* grad) {
+  double terms[6];
+  const int rc = octmc_eval_terms(p, level, disp, terms, grad);
+  if (f && (rc == OCTMC_OK || rc == OCTMC_ERR_NONFINITE)) *f = terms[4];
+  return rc;
+}
+
+int octmc_solve_level(octmc_problem* p, int level, double* disp, octmc_stats* st) {
+  if (!valid_level(p, level) || !disp) return OCTMC_ERR_INVALID_ARG;
+  return guarded([&] { return solve_impl(p, level, disp, st); });
+}
+
+int octmc_prolong(octmc_problem* p, int level, const double* coarse, double* fine) {
+  if (!valid_level(p, level) || level < 1 || !coarse || !fine) return OCTMC_ERR_INVALID_ARG;
+  return guarded([&] {
+    const LevelDev& C = p->lv[level].dev;
+    const LevelDev& F = p->lv[level - 1].dev;
+    CK(launch_prolong(coarse, C.w, C.h, fine, F.w, F.h, p->st));
+    CK(cudaStreamSynchronize(p->st));
+    return OCTMC_OK;
+  });
+}
+
+int octmc_solve_full(octmc_problem* p, double* disp_out, octmc_stats* st) {
+  if (!p || !disp_out) return OCTMC_ERR_INVALID_ARG;
+  return guarded([&] {
+    const int L = (int)p->lv.size();
+    ensure_solver(p);
+    // coarse-to-fine: the level field lives in p->xb's twin buffers; use dir
+    // as the coarse copy while prolonging
+    double* cur = disp_out;  // level-0 sized by contract
+    CK(cudaMemsetAsync(cur, 0, sizeof(double) * 6 * p->plane(L - 1), p->st));
+    int worst = OCTMC_OK;
+    for (int l = L - 1; l >= 0; l--) {
+      if (l != L - 1) {
+        CK(cudaMemcpyAsync(p->dir, cur, sizeof(double) * 6 * p->plane(l + 1), cudaMemcpyDeviceToDevice, p->st));
+        CK(launch_prolong(p->dir, p->lv[l + 1].dev.w, p->lv[l + 1].dev.h, cur, p->lv[l].dev.w,
+                          p->lv[l].dev.h, p->st));
+      }
+      octmc_stats s{};
+      const int rc = solve_impl(p, l, cur, &s);
+      if (st) st[L - 1 - l] = s;
+      if (rc < 0) return rc;
+      if (rc == OCTMC_NOT_CONVERGED) worst = rc;
+    }
+    return worst;
+  });
+}
+
+int octmc_level_data(const octmc_problem* p, int level, float* sx, float* sy, float* ax, float* ay, float* vx,
+                     float* vy) {
+  if (!valid_level(p, level)) return OCTMC_ERR_INVALID_ARG;
+  octmc_problem* q = const_cast<octmc_problem*>(p);
+  return guarded([&] {
+    const LevelDev& L = q->lv[level].dev;
+    const int64_t cols = (int64_t)L.w * L.h;
+    if (sx) CK(launch_unpad_depth(L.sx, cols, L.d, L.dp, sx, q->st));
+    if (sy) CK(launch_unpad_depth(L.sy, cols, L.d, L.dp, sy, q->st));
+    if (ax && L.ax) CK(cudaMemcpyAsync(ax, L.ax, sizeof(float) * cols, cudaMemcpyDeviceToDevice, q->st));
+    if (ay && L.ay) CK(cudaMemcpyAsync(ay, L.ay, sizeof(float) * cols, cudaMemcpyDeviceToDevice, q->st));
+    if (vx && L.vx) CK(cudaMemcpyAsync(vx, L.vx, sizeof(float) * L.h, cudaMemcpyDeviceToDevice, q->st));
+    if (vy && L.vy) CK(cudaMemcpyAsync(vy, L.vy, sizeof(float) * L.w, cudaMemcpyDeviceToDevice, q->st));
+    CK(cudaStreamSynchronize(q->st));
+    return OCTMC_OK;
+  });
+}
+
+int octmc_lbfgs_create(int64_t n, int m, void* stream, octmc_lbfgs** out) {
+  if (!out || n < 1 || m < 1 || m > 32) return OCTMC_ERR_INVALID_ARG;
+  *out = nullptr;
+  octmc_lbfgs* h = new (std::nothrow) octmc_lbfgs();
+  if (!h) return OCTMC_ERR_OOM;
+  const int rc = guarded([&] {
+    h->init(n, m, (cudaStream_t)stream);
+    CK(cudaStreamSynchronize(h->st));
+    return OCTMC_OK;
+  });
+  if (rc != OCTMC_OK) {
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return OCTMC_OK;
+}
+
+void octmc_lbfgs_destroy(octmc_lbfgs* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->st);
+  delete h;
+}
+
+int octmc_lbfgs_push(octmc_lbfgs* h, const double* s, const double* y) {
+  if (!h || !s || !y) return OCTMC_ERR_INVALID_ARG;
+  return guarded([&] {
+    CK(cudaMemcpyAsync(h->S[h->spare], s, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(h->Y[h->spare], y, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->st));
+    return h->prepare(nullptr, true);
+  });
+}
+
+int octmc_lbfgs_direction(octmc_lbfgs* h, const double* g, double* dir, double* gtd) {
+  if (!h || !g || !dir) return OCTMC_ERR_INVALID_ARG;
+  return guarded([&] {
+    h->prepare(g, false);
+    const double v = h->direction(g, dir);
+    CK(cudaStreamSynchronize(h->st));
+    if (gtd) *gtd = v;
+    return OCTMC_OK;
+  });
+}
+
+int octmc_lbfgs_reset(octmc_lbfgs* h) {
+  if (!h) return OCTMC_ERR_INVALID_ARG;
+  h->reset();
+  return OCTMC_OK;
+}
+
+int octmc_profile_enable(octmc_problem* p, int enable) {
+  if (!p) return OCTMC_ERR_INVALID_ARG;
+  return guarded([&] {
+    if (enable && !p->ev0) {
+      CK(cudaEventCreate(&p->ev0));
+      CK(cudaEventCreate(&p->ev1));
+    }
+    p->profile = enable != 0;
+    p->prof_ms = 0.0;
+    p->prof_count = 0;
+    p->prof_pending = false;
+    return OCTMC_OK;
+  });
+}
+
+int octmc_profile_read(octmc_problem* p, double* total_ms, long long* launches) {
+  if (!p) return OCTMC_ERR_INVALID_ARG;
+  if (total_ms) *total_ms = p->prof_ms;
+  if (launches) *launches = p->prof_count;
+  return OCTMC_OK;
+}
+
+const char* octmc_status_string(int code) {
+  switch (code) {
+    case OCTMC_OK: return "ok";
+    case OCTMC_NOT_CONVERGED: return "not converged (iteration cap)";
+    case OCTMC_ERR_INVALID_ARG: return "invalid argument";
+    case OCTMC_ERR_OOM: return "out of device memory";
+    case OCTMC_ERR_CUDA: return "CUDA error";
+    case OCTMC_ERR_NONFINITE: return "objective is not finite";
+    case OCTMC_ERR_TIMEOUT: return "device wait timed out";
+    case OCTMC_ERR_UNSUPPORTED: return "unsupported (needs an sm_103a device / dtype not built)";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,148 @@
+// Internal declarations shared by the CUDA translation units of liboctmc.
+// Device helpers, kernel argument structs and launcher prototypes.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "octmc.h"
+
+namespace octmc {
+
+constexpr int kWarp = 32;
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ int clampi(int i, int n) { return i < 0 ? 0 : (i >= n ? n - 1 : i); }
+
+// Keys cubic-convolution kernel with a = -1/2 (the Catmull-Rom spline, i.e.
+// cubic Hermite interpolation with central-difference tangents): weights of
+// the samples at n-1, n, n+1, n+2 for a point n + t, expanded in powers of t
+// and evaluated by Horner's rule, plus their t-derivatives.
+__device__ __forceinline__ void keys_weights(float t, float w[4], float dw[4]) {
+  w[0] = t * fmaf(t, fmaf(-0.5f, t, 1.0f), -0.5f);
+  w[1] = fmaf(t * t, fmaf(1.5f, t, -2.5f), 1.0f);
+  w[2] = t * fmaf(t, fmaf(-1.5f, t, 2.0f), 0.5f);
+  w[3] = (t * t) * fmaf(0.5f, t, -0.5f);
+  dw[0] = fmaf(t, fmaf(-1.5f, t, 2.0f), -0.5f);
+  dw[1] = t * fmaf(4.5f, t, -5.0f);
+  dw[2] = fmaf(t, fmaf(-4.5f, t, 4.0f), 0.5f);
+  dw[3] = t * fmaf(1.5f, t, -1.0f);
+}
+
+// Splits a sample coordinate u on a grid of n samples into floor(u) and a
+// float fraction.  With edge replication the interpolant is constant for
+// u < -1 and for u >= n, so u is first clamped to [-4, n + 3] (this also
+// maps NaN to a finite coordinate and keeps the integer in range).
+__device__ __forceinline__ void split_coord(double u, int n, int* base, float* t) {
+  u = fmin(fmax(u, -4.0), (double)n + 3.0);
+  double f = floor(u);
+  *base = (int)f;
+  *t = (float)(u - f);
+}
+
+// Deterministic warp sum (xor butterfly; every lane ends with the total).
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------- level data
+// One pyramid level on the device.  Volumes are [h][w][dp] with dp = d
+// rounded up to a multiple of 4; the pad samples [d, dp) repeat sample d-1,
+// so aligned 4-sample groups inside [0, dp) read clamp-to-edge values.
+struct LevelDev {
+  int w, h, d, dp;
+  float* sx;
+  float* sy;
+  float* ax;  // [h][w] or null
+  float* ay;
+  float* vx;  // [h] or null
+  float* vy;  // [w] or null
+  // time-ordered chain of each volume (the temporal regulariser's pairs):
+  // for A-scan p, the previous/next A-scan in acquisition order (-1: none)
+  // and the weight of the pair (prev, p) / (p, next).
+  int* prev[2];
+  int* next[2];
+  double* wprev[2];
+  double* wnext[2];
+};
+
+// Arguments of the data-term kernel (Eq. 2-8 per A-scan).
+struct DataArgs {
+  LevelDev L;
+  const double* disp;  // [2][3][h][w]
+  double* str_out;     // [h*w]: (1 - delta) sum_k L(R_ijk)
+  double* ang_out;     // [h*w]: delta d L(R_ij(A))
+  double* grad;        // [2][3][h][w] or null
+  double eta;          // Eq. 9
+  double delta0;       // Eq. 8 (0 without angiography)
+  float eps_h;         // Eq. 4
+  int loss;            // octmc_loss
+};
+
+// Output of the final reduction of one evaluation.
+struct EvalResult {
+  double terms[6];  // S^str, S^ang, R, M, f, eta
+  double gdir;      // grad . dir (line search), 0 if no dir
+  double msum[3];   // sum over both volumes of each displacement component
+};
+
+struct RegArgs {
+  LevelDev L;
+  const double* disp;
+  double* grad;           // may be null
+  const double* dir;      // may be null: then gdir = 0
+  const double* str_in;   // [h*w]
+  const double* ang_in;   // [h*w]
+  double alpha, eps_r, mu, eta;
+  EvalResult* result;     // device
+  double* partials;       // [grid][8] scratch
+  unsigned* counter;      // zero-initialised, reset by the last block
+};
+
+// ---------------------------------------------------------------- launchers
+cudaError_t launch_data(const DataArgs& a, cudaStream_t s);
+cudaError_t launch_msum(const double* disp, int64_t plane, EvalResult* res, double* partials,
+                        unsigned* counter, cudaStream_t s);
+cudaError_t launch_reg(const RegArgs& a, cudaStream_t s);
+int reg_grid_blocks(int64_t n_ascans);
+int msum_grid_blocks();
+
+cudaError_t launch_pad_depth(float* vol, int64_t columns, int d, int dp, cudaStream_t s);
+cudaError_t launch_pyr_volume(const float* in, int w, int h, int d, int dp, float* out, int w2,
+                              int h2, int d2, int dp2, cudaStream_t s);
+cudaError_t launch_pyr_image(const float* in, int w, int h, float* out, cudaStream_t s);
+cudaError_t launch_pyr_line(const float* in, int n, float* out, cudaStream_t s);
+cudaError_t launch_prolong(const double* coarse, int wc, int hc, double* fine, int wf, int hf,
+                           cudaStream_t s);
+cudaError_t launch_unpad_depth(const float* vol, int64_t columns, int d, int dp, float* out,
+                               cudaStream_t s);
+
+// L-BFGS vector kernels (float64).
+constexpr int kMaxDots = 80;
+constexpr int kMaxVecs = 72;
+struct DotList {
+  const double* a[kMaxDots];
+  const double* b[kMaxDots];
+  int n;
+};
+struct LinComb {
+  const double* v[kMaxVecs];
+  double c[kMaxVecs];
+  int n;
+};
+int dots_grid_blocks(int64_t n);
+cudaError_t launch_dots(const DotList& dl, int64_t n, const double* maxabs_of, double* partials,
+                        unsigned* counter, double* out, cudaStream_t s);
+cudaError_t launch_lincomb(const LinComb& lc, int64_t n, double* out, cudaStream_t s);
+cudaError_t launch_sub2(const double* x1, const double* x0, const double* g1, const double* g0,
+                        double* s_out, double* y_out, int64_t n, cudaStream_t st);
+cudaError_t launch_axpy(const double* x, double a, const double* d, double* out, int64_t n,
+                        cudaStream_t s);
+
+}  // namespace octmc

@@ -1,0 +1,207 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (GPU only).
+
+Tolerances (float data term, double reductions): objective 1e-5 relative,
+gradient 1e-4 relative L2 (over the whole field), pyramid bit-exact, the
+L-BFGS direction 1e-10 relative (double arithmetic).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from octsynth import make_config, make_pair, true_displacement
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+F_TOL = 1e-5
+G_TOL = 1e-4
+
+
+def gpu_problem(p, **kw):
+    import paper_2010_06931_gb300 as octmc
+    return octmc.Problem(p["sx"], p["sy"], p["tx"], p["ty"], p.get("ax"), p.get("ay"), p.get("vx"),
+                         p.get("vy"), **kw)
+
+
+def cpu_problem(p, **kw):
+    kw = {k: v for k, v in kw.items() if k in ("alpha", "delta0", "eps_h", "eps_r", "mu", "loss")}
+    if kw.get("mu", 0.0) == 0.0:
+        kw["mu"] = None
+    return O.OracleProblem(p["sx"], p["sy"], p["tx"], p["ty"], p.get("ax"), p.get("ay"), p.get("vx"),
+                           p.get("vy"), **kw)
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def compare_eval(p, D, eta=0.8, **kw):
+    G = gpu_problem(p, **kw)
+    C = cpu_problem(p, **kw)
+    G.set_eta(0, eta)
+    C.eta = eta
+    g = torch.zeros(G.disp_shape(0), dtype=torch.float64, device="cuda")
+    tg = G.eval_terms(0, cuda(D), g)
+    fc, gc, tc = C.eval(D)
+    assert abs(tg[4] - fc) <= F_TOL * abs(fc), (tg, tc)
+    for t in range(4):
+        assert abs(tg[t] - tc[t]) <= F_TOL * max(abs(tc[t]), 1e-12 * abs(fc)), (t, tg, tc)
+    err = rel_l2(g.cpu().numpy(), gc)
+    assert err <= G_TOL, err
+    return tg, g.cpu().numpy(), tc, gc
+
+
+@pytest.fixture(scope="module")
+def c1():
+    return make_config("c1")
+
+
+@pytest.mark.parametrize("loss", [0, 1])
+def test_eval_c1_random_displacements(c1, loss):
+    p, cfg = c1
+    rng = np.random.default_rng(11)
+    for scale in (0.0, 0.6, 3.0):
+        D = rng.normal(0.0, scale, (2, 3, cfg["h"], cfg["w"]))
+        compare_eval(p, D, loss=loss)
+
+
+def test_eval_c1_at_truth_and_oct_only(c1):
+    p, cfg = c1
+    T, _ = true_displacement(p, cfg["w"], cfg["h"])
+    compare_eval(p, T)
+    q = dict(p)
+    for k in ("ax", "ay", "vx", "vy"):
+        q[k] = None
+    compare_eval(q, T, delta0=0.0)
+
+
+@pytest.mark.parametrize("shape", [(29, 37, 245), (5, 3, 1), (1, 7, 6), (8, 1, 117), (13, 11, 4)])
+def test_eval_ragged_shapes(shape):
+    # depth not a multiple of 4 nor of the 116-sample blocks, odd grids, degenerate axes
+    h, w, d = shape
+    p = make_pair(w, h, d, n_layers=4, n_slabs=1, n_saccades=1, max_saccade=2.0, drift_sigma=0.05, seed=3)
+    rng = np.random.default_rng(5)
+    D = rng.normal(0.0, 1.5, (2, 3, h, w))
+    compare_eval(p, D)
+    compare_eval(p, D, loss=1, alpha=0.3, eps_r=0.2, mu=0.05)
+
+
+def test_eval_far_outside_the_grid():
+    # displacements beyond every edge: all taps are edge samples (clamp-to-edge)
+    h, w, d = 9, 10, 23
+    p = make_pair(w, h, d, n_layers=4, n_slabs=1, n_saccades=1, max_saccade=2.0, drift_sigma=0.05, seed=4)
+    D = np.zeros((2, 3, h, w))
+    D[0, 0] = 1e4
+    D[1, 1] = -3e5
+    D[0, 2] = -77.3
+    D[1, 2] = 1e9
+    compare_eval(p, D)
+
+
+def test_identical_inputs_give_exact_zero(c1):
+    p, cfg = c1
+    q = dict(p)
+    q["sy"], q["ay"] = p["sx"].copy(), p["ax"].copy()
+    G = gpu_problem(q)
+    g = torch.full(G.disp_shape(0), 7.0, dtype=torch.float64, device="cuda")
+    t = G.eval_terms(0, G.zeros(0), g)
+    assert np.all(t[:5] == 0.0)
+    assert torch.count_nonzero(g).item() == 0
+
+
+def test_nonfinite_displacement_is_reported(c1):
+    import paper_2010_06931_gb300 as octmc
+    p, cfg = c1
+    G = gpu_problem(p)
+    D = G.zeros(0)
+    D[0, 0, 3, 4] = float("nan")
+    with pytest.raises(octmc.OctmcError) as e:
+        G.eval_terms(0, D)
+    assert e.value.code == -4
+
+
+def test_eval_is_deterministic(c1):
+    p, cfg = c1
+    G = gpu_problem(p)
+    D = cuda(np.random.default_rng(1).normal(0, 1.0, G.disp_shape(0)))
+    g1, g2 = torch.empty_like(D), torch.empty_like(D)
+    t1 = G.eval_terms(0, D, g1)
+    t2 = G.eval_terms(0, D, g2)
+    assert np.array_equal(t1, t2) and torch.equal(g1, g2)
+
+
+def test_eta_parity(c1):
+    p, cfg = c1
+    G, C = gpu_problem(p), cpu_problem(p)
+    D = np.random.default_rng(2).normal(0, 0.5, G.disp_shape(0))
+    assert G.compute_eta(0, cuda(D)) == pytest.approx(C.compute_eta(D), rel=F_TOL)
+    q = dict(p)
+    q["ax"] = q["ay"] = None
+    assert gpu_problem(q).compute_eta(0, cuda(D)) == 1.0
+
+
+def test_pyramid_bit_exact():
+    p = make_pair(37, 29, 51, n_layers=4, n_slabs=1, n_saccades=1, max_saccade=2.0, drift_sigma=0.05, seed=8)
+    G = gpu_problem(p, levels=3)
+    C = cpu_problem(p).pyramid(3)
+    for l in range(3):
+        got = {k: v.cpu().numpy() for k, v in G.level_data(l).items()}
+        for k in ("sx", "sy", "ax", "ay", "vx", "vy"):
+            ref = getattr(C[l], k)
+            assert got[k].shape == ref.shape, (l, k)
+            assert np.array_equal(got[k], ref), (l, k)
+
+
+def test_prolong_parity():
+    p = make_pair(37, 29, 8, n_layers=4, n_slabs=1, n_saccades=1, max_saccade=2.0, drift_sigma=0.05, seed=8)
+    G = gpu_problem(p, levels=2)
+    w1, h1, _ = G.level_shape(1)
+    c = np.random.default_rng(3).normal(size=(2, 3, h1, w1))
+    fine = G.prolong(1, cuda(c)).cpu().numpy()
+    ref = O.prolong(c, 29, 37)
+    assert np.allclose(fine, ref, rtol=1e-14, atol=1e-14)
+
+
+def test_lbfgs_direction_parity():
+    import paper_2010_06931_gb300 as octmc
+    rng = np.random.default_rng(6)
+    n = 5000
+    A = rng.uniform(0.5, 3.0, size=n)  # diagonal SPD curvature
+    S = [rng.normal(size=n) for _ in range(11)]
+    Y = [A * s + 0.01 * rng.normal(size=n) for s in S]
+    g = rng.normal(size=n)
+    H = octmc.Lbfgs(n, m=8)
+    for s, y in zip(S, Y):
+        assert H.push(cuda(s), cuda(y)) == 0
+    d, gtd = H.direction(cuda(g))
+    ref = O.lbfgs_direction(S[-8:], Y[-8:], g)  # the last 8 pairs are kept
+    assert rel_l2(d.cpu().numpy(), ref) < 1e-10
+    assert gtd == pytest.approx(float(g @ ref), rel=1e-10)
+    # a pair with negative curvature is rejected and changes nothing
+    assert H.push(cuda(S[0]), cuda(-Y[0])) == 1
+    d2, _ = H.direction(cuda(g))
+    assert torch.equal(d, d2)
+    H.reset()
+    d3, gtd3 = H.direction(cuda(g))
+    assert np.array_equal(d3.cpu().numpy(), -g) and gtd3 == pytest.approx(-(g @ g), rel=1e-12)
+
+
+@pytest.mark.parametrize("loss", [1, 0])
+def test_solve_level_parity_c1(c1, loss):
+    # identical algorithm and constants on both sides; compare the solutions
+    p, cfg = c1
+    kw = dict(loss=loss, alpha=1.0)
+    G = gpu_problem(p, max_iter=150, **kw)
+    C = cpu_problem(p, **kw)
+    D = G.zeros(0)
+    st = G.solve_level(0, D)
+    Dc, stc = C.solve_level(np.zeros(G.disp_shape(0)), max_iter=150)
+    Dg = D.cpu().numpy()
+    rms = float(np.sqrt(((Dg - Dc) ** 2).mean()))
+    assert st["eta"] == pytest.approx(stc["eta"], rel=F_TOL)
+    assert rms <= 0.05, (rms, st, stc)
+    assert st["f"] == pytest.approx(stc["f"], rel=1e-3)
