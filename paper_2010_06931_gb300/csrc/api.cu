@@ -57,7 +57,7 @@ int pad4(int d) { return (d + 3) & ~3; }
 // Time-ordered chain of the A-scans of one volume: prev/next neighbour in
 // acquisition order and the weight dt_min / dt of each pair (ties weigh 1).
 void build_chain(const std::vector<double>& t, std::vector<int>& prev, std::vector<int>& next,
-                 std::vector<double>& wprev, std::vector<double>& wnext) {
+                 std::vector<float>& wprev, std::vector<float>& wnext) {
   const int n = (int)t.size();
   std::vector<int> order(n);
   std::iota(order.begin(), order.end(), 0);
@@ -69,16 +69,16 @@ void build_chain(const std::vector<double>& t, std::vector<int>& prev, std::vect
   }
   prev.assign(n, -1);
   next.assign(n, -1);
-  wprev.assign(n, 0.0);
-  wnext.assign(n, 0.0);
+  wprev.assign(n, 0.f);
+  wnext.assign(n, 0.f);
   for (int m = 0; m + 1 < n; m++) {
     const int a = order[m], b = order[m + 1];
     const double dt = t[b] - t[a];
     const double om = std::isinf(dtmin) ? 1.0 : dtmin / std::max(dt, dtmin);
     next[a] = b;
-    wnext[a] = om;
+    wnext[a] = (float)om;
     prev[b] = a;
-    wprev[b] = om;
+    wprev[b] = (float)om;
   }
 }
 
@@ -298,8 +298,9 @@ struct octmc_problem {
   bool have_ang = false;
   std::vector<Level> lv;
   // evaluation workspace (sized for level 0)
-  double* str = nullptr;
-  double* ang = nullptr;
+  float* str = nullptr;
+  float* ang = nullptr;
+  float* gdata = nullptr;  // data-term gradient (float), consumed by reg_kernel
   double* partials = nullptr;
   unsigned* counters = nullptr;  // [0] msum, [1] reg
   EvalResult* res = nullptr;
@@ -330,7 +331,7 @@ struct octmc_problem {
         dfree(d.prev[V]); dfree(d.next[V]); dfree(d.wprev[V]); dfree(d.wnext[V]);
       }
     }
-    dfree(str); dfree(ang); dfree(partials); dfree(counters); dfree(res);
+    dfree(str); dfree(ang); dfree(gdata); dfree(partials); dfree(counters); dfree(res);
     if (res_host) cudaFreeHost(res_host);
     dfree(x); dfree(g); dfree(xt); dfree(gt); dfree(xb); dfree(gb); dfree(dir);
     delete opt;
@@ -430,12 +431,12 @@ void create_impl(octmc_problem* P) {
     }
     for (int V = 0; V < 2; V++) {
       std::vector<int> pv, nx;
-      std::vector<double> wp, wn;
+      std::vector<float> wp, wn;
       build_chain(V == 0 ? tx : ty, pv, nx, wp, wn);
       X.prev[V] = dalloc<int>((size_t)cols);
       X.next[V] = dalloc<int>((size_t)cols);
-      X.wprev[V] = dalloc<double>((size_t)cols);
-      X.wnext[V] = dalloc<double>((size_t)cols);
+      X.wprev[V] = dalloc<float>((size_t)cols);
+      X.wnext[V] = dalloc<float>((size_t)cols);
       upload_host(P, pv, X.prev[V]);
       upload_host(P, nx, X.next[V]);
       upload_host(P, wp, X.wprev[V]);
@@ -448,8 +449,9 @@ void create_impl(octmc_problem* P) {
     d = half_up(d);
   }
   const int64_t n0 = P->plane(0);
-  P->str = dalloc<double>((size_t)n0);
-  P->ang = dalloc<double>((size_t)n0);
+  P->str = dalloc<float>((size_t)n0);
+  P->ang = dalloc<float>((size_t)n0);
+  P->gdata = dalloc<float>((size_t)6 * n0);
   P->partials = dalloc<double>((size_t)8 * std::max(reg_grid_blocks(n0), msum_grid_blocks()));
   P->counters = dalloc<unsigned>(2);
   CK(cudaMemsetAsync(P->counters, 0, 2 * sizeof(unsigned), P->st));
@@ -480,7 +482,7 @@ void eval_impl(octmc_problem* P, int l, const double* disp, double* grad, const 
   A.disp = disp;
   A.str_out = P->str;
   A.ang_out = P->ang;
-  A.grad = grad;
+  A.grad = grad ? P->gdata : nullptr;
   A.eta = eta;
   A.delta0 = P->have_ang ? delta0 : 0.0;
   A.eps_h = (float)P->desc.eps_h;
@@ -495,6 +497,7 @@ void eval_impl(octmc_problem* P, int l, const double* disp, double* grad, const 
   R.L = Lv.dev;
   R.disp = disp;
   R.grad = grad;
+  R.gdata = P->gdata;
   R.dir = dir;
   R.str_in = P->str;
   R.ang_in = P->ang;

@@ -28,15 +28,110 @@ __device__ __forceinline__ void keys_weights(float t, float w[4], float dw[4]) {
   dw[3] = t * fmaf(1.5f, t, -1.0f);
 }
 
-// Splits a sample coordinate u on a grid of n samples into floor(u) and a
-// float fraction.  With edge replication the interpolant is constant for
-// u < -1 and for u >= n, so u is first clamped to [-4, n + 3] (this also
-// maps NaN to a finite coordinate and keeps the integer in range).
-__device__ __forceinline__ void split_coord(double u, int n, int* base, float* t) {
-  u = fmin(fmax(u, -4.0), (double)n + 3.0);
-  double f = floor(u);
-  *base = (int)f;
-  *t = (float)(u - f);
+// Exact split of u = off + v, v a double given by its bit pattern and off an
+// integer, into floor(u) and the fraction u - floor(u) as a float (mantissa
+// truncated to 24 bits), after clamping u into the integer range [lo, hi].
+// Integer instructions only: double arithmetic runs at 1/64 of the float
+// rate on this GPU and has a long latency.  NaN maps to lo, -inf to lo, +inf
+// to hi, |v| >= 2^31 to the nearer bound; float-subnormal fractions to 0.
+__device__ __forceinline__ void split_exact(unsigned long long bits, int off, int lo, int hi, int* base,
+                                            float* t) {
+  const unsigned h32 = (unsigned)(bits >> 32);
+  const bool neg = (h32 >> 31) != 0;
+  const int ex = (int)((h32 >> 20) & 0x7ffu);
+  unsigned long long m = bits & 0xFFFFFFFFFFFFFull;
+  if (ex == 0x7ff) {  // inf or NaN
+    *base = (m == 0ull && !neg) ? hi : lo;
+    *t = 0.f;
+    return;
+  }
+  if (ex >= 1023 + 31) {
+    *base = neg ? lo : hi;
+    *t = 0.f;
+    return;
+  }
+  int sh;  // |v| = m * 2^-sh, sh >= 22
+  if (ex == 0) {
+    sh = 1074;
+  } else {
+    m |= 1ull << 52;
+    sh = 1075 - ex;
+  }
+  unsigned long long ip, fb;
+  if (sh >= 64) {
+    ip = 0ull;
+    fb = m;
+  } else {
+    ip = m >> sh;
+    fb = m & ((1ull << sh) - 1ull);
+  }
+  float f = 0.f;  // fb * 2^-sh, built from its bits
+  if (fb != 0ull) {
+    const int lz = __clzll((long long)fb);
+    const int pos = 63 - lz;  // leading bit of fb
+    const unsigned mant = (unsigned)((fb << lz) >> 40);  // top 24 bits, leading 1 included
+    const int ef = pos - sh + 127;
+    if (ef > 0) f = __uint_as_float(((unsigned)ef << 23) | (mant & 0x7fffffu));
+  }
+  int b;
+  float tt;
+  const int ipi = (int)ip;
+  if (!neg) {
+    b = off + ipi;
+    tt = f;
+  } else if (f > 0.f) {
+    b = off - ipi - 1;
+    tt = 1.0f - f;
+  } else {
+    b = off - ipi;
+    tt = 0.f;
+  }
+  if (b < lo) {
+    b = lo;
+    tt = 0.f;
+  } else if (b > hi || (b == hi && tt > 0.f)) {
+    b = hi;
+    tt = 0.f;
+  }
+  *base = b;
+  *t = tt;
+}
+
+// Float to double by assembling the bits (exact for normal floats and zero;
+// float subnormals become signed zero; inf and NaN stay inf and NaN).
+__device__ __forceinline__ double widen_exact(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned sign = u & 0x80000000u;
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned m = u & 0x7fffffu;
+  unsigned hi, lo;
+  if (e == 0u) {
+    hi = sign;
+    lo = 0u;
+  } else if (e == 255u) {
+    hi = sign | 0x7ff00000u | (m >> 3);
+    lo = m << 29;
+  } else {
+    hi = sign | ((e + 896u) << 20) | (m >> 3);
+    lo = m << 29;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// Double to float by truncating the mantissa (integer instructions only):
+// values below the float normal range become signed zero, values beyond it
+// infinity; NaN stays NaN.
+__device__ __forceinline__ float narrow_trunc(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned h = (unsigned)(b >> 32);
+  const unsigned sign = h & 0x80000000u;
+  const int e = (int)((h >> 20) & 0x7ffu);
+  const unsigned mant = (unsigned)((b >> 29) & 0x7fffffu);
+  if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (mant | ((b & 0xFFFFFFFFFFFFFull) ? 1u : 0u)));
+  const int ef = e - 1023 + 127;
+  if (ef <= 0) return __uint_as_float(sign);
+  if (ef >= 255) return __uint_as_float(sign | 0x7f800000u);
+  return __uint_as_float(sign | ((unsigned)ef << 23) | mant);
 }
 
 // Deterministic warp sum (xor butterfly; every lane ends with the total).
@@ -68,17 +163,17 @@ struct LevelDev {
   // and the weight of the pair (prev, p) / (p, next).
   int* prev[2];
   int* next[2];
-  double* wprev[2];
-  double* wnext[2];
+  float* wprev[2];
+  float* wnext[2];
 };
 
 // Arguments of the data-term kernel (Eq. 2-8 per A-scan).
 struct DataArgs {
   LevelDev L;
   const double* disp;  // [2][3][h][w]
-  double* str_out;     // [h*w]: (1 - delta) sum_k L(R_ijk)
-  double* ang_out;     // [h*w]: delta d L(R_ij(A))
-  double* grad;        // [2][3][h][w] or null
+  float* str_out;      // [h*w]: (1 - delta) sum_k L(R_ijk)
+  float* ang_out;      // [h*w]: delta d L(R_ij(A))
+  float* grad;         // [2][3][h][w] data-term gradient, or null
   double eta;          // Eq. 9
   double delta0;       // Eq. 8 (0 without angiography)
   float eps_h;         // Eq. 4
@@ -95,10 +190,11 @@ struct EvalResult {
 struct RegArgs {
   LevelDev L;
   const double* disp;
-  double* grad;           // may be null
+  double* grad;           // may be null: output gradient (data + R + M)
+  const float* gdata;     // data-term gradient from the data kernel (if grad)
   const double* dir;      // may be null: then gdir = 0
-  const double* str_in;   // [h*w]
-  const double* ang_in;   // [h*w]
+  const float* str_in;    // [h*w]
+  const float* ang_in;    // [h*w]
   double alpha, eps_r, mu, eta;
   EvalResult* result;     // device
   double* partials;       // [grid][8] scratch

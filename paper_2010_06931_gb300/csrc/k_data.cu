@@ -38,22 +38,41 @@ struct Vol {
   int bx, by;          // floor of the transverse coordinates
 };
 
-__device__ __forceinline__ void setup_vol(Vol& V, const float* vol, const LevelDev& L, int i, int j,
-                                          double dx, double dy, double dz) {
-  float tx, ty, tz;
-  split_coord((double)i + dx, L.w, &V.bx, &tx);
-  split_coord((double)j + dy, L.h, &V.by, &ty);
-  // Along depth every output k shares floor(dz) and the fraction; beyond
-  // |dz| > d + 4 all taps are edge samples, so dz is clamped to +-(d + 8).
-  double dzc = fmin(fmax(dz, -(double)L.d - 8.0), (double)L.d + 8.0);
-  double fz = floor(dzc);
-  int kz0 = (int)fz;
-  tz = (float)(dzc - fz);
+// Coordinate split of the 6 displacement values of A-scan (i, j) by lanes
+// 0..5 (lane = 3 V + c), broadcast to the warp: floor(u) and the float
+// fraction for u = i + dx and u = j + dy clamped to [-4, n + 3] (beyond that
+// every tap is an edge sample) and u = dz clamped to +-(d + 8) (all depth
+// taps are then edge samples).  Integer arithmetic only (split_exact).
+__device__ __forceinline__ void split_displacement(const double* disp, int64_t nasc, int64_t p, int i,
+                                                   int j, const LevelDev& L, int lane, int base[6],
+                                                   float frac[6]) {
+  int b = 0;
+  float t = 0.f;
+  if (lane < 6) {
+    const int c = lane % 3;
+    const unsigned long long bits =
+        (unsigned long long)__double_as_longlong(disp[(int64_t)lane * nasc + p]);
+    if (c == 0) split_exact(bits, i, -4, L.w + 3, &b, &t);
+    else if (c == 1) split_exact(bits, j, -4, L.h + 3, &b, &t);
+    else split_exact(bits, 0, -L.d - 8, L.d + 8, &b, &t);
+  }
+#pragma unroll
+  for (int c = 0; c < 6; c++) {
+    base[c] = __shfl_sync(0xffffffffu, b, c);
+    frac[c] = __shfl_sync(0xffffffffu, t, c);
+  }
+}
+
+__device__ __forceinline__ void setup_vol(Vol& V, const float* vol, const LevelDev& L, const int base[3],
+                                          const float frac[3]) {
+  V.bx = base[0];
+  V.by = base[1];
+  const int kz0 = base[2];
   V.q = kz0 >> 2;  // arithmetic shift: floor division by 4
   V.r = kz0 & 3;
-  keys_weights(tx, V.wx, V.dwx);
-  keys_weights(ty, V.wy, V.dwy);
-  keys_weights(tz, V.wz, V.dwz);
+  keys_weights(frac[0], V.wx, V.dwx);
+  keys_weights(frac[1], V.wy, V.dwy);
+  keys_weights(frac[2], V.wz, V.dwz);
   const unsigned nq = (unsigned)(L.dp >> 2);
 #pragma unroll
   for (int a = 0; a < 4; a++) {
@@ -158,7 +177,10 @@ __device__ __forceinline__ void sample_block(const Vol& V, int kb, int lane, int
   }
 }
 
-__global__ void __launch_bounds__(kWarpsPerBlock * kWarp)
+#ifndef OCTMC_DATA_MINB
+#define OCTMC_DATA_MINB 2
+#endif
+__global__ void __launch_bounds__(kWarpsPerBlock * kWarp, OCTMC_DATA_MINB)
 data_kernel(const DataArgs A) {
   const LevelDev& L = A.L;
   const int lane = threadIdx.x & 31;
@@ -167,15 +189,12 @@ data_kernel(const DataArgs A) {
   if (p >= nasc) return;  // warp-uniform
   const int i = (int)(p % L.w), j = (int)(p / L.w);
 
-  double dX[3], dY[3];
-#pragma unroll
-  for (int c = 0; c < 3; c++) {
-    dX[c] = A.disp[(0 * 3 + c) * nasc + p];
-    dY[c] = A.disp[(1 * 3 + c) * nasc + p];
-  }
+  int base[6];
+  float frac[6];
+  split_displacement(A.disp, nasc, p, i, j, L, lane, base, frac);
   Vol VX, VY;
-  setup_vol(VX, L.sx, L, i, j, dX[0], dX[1], dX[2]);
-  setup_vol(VY, L.sy, L, i, j, dY[0], dY[1], dY[2]);
+  setup_vol(VX, L.sx, L, base, frac);
+  setup_vol(VY, L.sy, L, base + 3, frac + 3);
 
   const float inv_eps = 1.0f / A.eps_h;
   const bool ssd = (A.loss == OCTMC_LOSS_SSD);
@@ -215,81 +234,94 @@ data_kernel(const DataArgs A) {
   }
 #pragma unroll
   for (int c = 0; c < 7; c++) acc[c] = warp_sum(acc[c]);
-  if (lane != 0) return;
 
-  // ---- per-A-scan scalars (Eq. 6-8), lane 0
-  const double d = (double)L.d;
-  double vtx = 1.0, dvtx = 0.0, vty = 1.0, dvty = 0.0;
-  if (L.vx) {  // Eq. 7: X validity along y at j + dy^X (same weights as S^X in y)
-    float v = 0.f, dv = 0.f;
+  // ---- per-A-scan scalars (Eq. 6-8), float, every lane
+  float vtx = 1.f, dvtx = 0.f, vty = 1.f, dvty = 0.f;
+  if (L.vx) {  // Eq. 7: X validity along y at j + dy^X (the weights of S^X in y)
+    vtx = 0.f;
 #pragma unroll
     for (int b = 0; b < 4; b++) {
       const float s = L.vx[clampi(VX.by - 1 + b, L.h)];
-      v = fmaf(VX.wy[b], s, v);
-      dv = fmaf(VX.dwy[b], s, dv);
+      vtx = fmaf(VX.wy[b], s, vtx);
+      dvtx = fmaf(VX.dwy[b], s, dvtx);
     }
-    vtx = v; dvtx = dv;
   }
   if (L.vy) {  // Y validity along x at i + dx^Y
-    float v = 0.f, dv = 0.f;
+    vty = 0.f;
 #pragma unroll
     for (int a = 0; a < 4; a++) {
       const float s = L.vy[clampi(VY.bx - 1 + a, L.w)];
-      v = fmaf(VY.wx[a], s, v);
-      dv = fmaf(VY.dwx[a], s, dv);
+      vty = fmaf(VY.wx[a], s, vty);
+      dvty = fmaf(VY.dwx[a], s, dvty);
     }
-    vty = v; dvty = dv;
   }
-  const double delta0 = A.delta0;
-  const double delta = delta0 * vtx * vty;  // Eq. 8
+  const float delta0 = (float)A.delta0;
+  const float delta = delta0 * vtx * vty;  // Eq. 8
+  const float d = (float)L.d;
 
-  double La = 0.0, dLa = 0.0, gAX[2] = {0.0, 0.0}, gAY[2] = {0.0, 0.0};
-  if (L.ax) {  // Eq. 6: en-face residual at the displaced transverse positions
-    float aX = 0.f, aXx = 0.f, aXy = 0.f, aY = 0.f, aYx = 0.f, aYy = 0.f;
+  float La = 0.f, dLa = 0.f, aXx = 0.f, aXy = 0.f, aYx = 0.f, aYy = 0.f;
+  if (L.ax) {
+    // Eq. 6: the 16 taps of A^X (lanes 0..15) and of A^Y (lanes 16..31) at
+    // the displaced transverse positions, then a butterfly within each half
+    const bool isX = lane < 16;
+    const float* img = isX ? L.ax : L.ay;
+    const int a = lane & 3, b = (lane >> 2) & 3;
+    float wa = 0.f, dwa = 0.f, wb = 0.f, dwb = 0.f;
 #pragma unroll
-    for (int b = 0; b < 4; b++) {
-      const int rX = clampi(VX.by - 1 + b, L.h), rY = clampi(VY.by - 1 + b, L.h);
-#pragma unroll
-      for (int a = 0; a < 4; a++) {
-        const float sX = L.ax[(int64_t)rX * L.w + clampi(VX.bx - 1 + a, L.w)];
-        const float sY = L.ay[(int64_t)rY * L.w + clampi(VY.bx - 1 + a, L.w)];
-        aX = fmaf(VX.wx[a] * VX.wy[b], sX, aX);
-        aXx = fmaf(VX.dwx[a] * VX.wy[b], sX, aXx);
-        aXy = fmaf(VX.wx[a] * VX.dwy[b], sX, aXy);
-        aY = fmaf(VY.wx[a] * VY.wy[b], sY, aY);
-        aYx = fmaf(VY.dwx[a] * VY.wy[b], sY, aYx);
-        aYy = fmaf(VY.wx[a] * VY.dwy[b], sY, aYy);
-      }
+    for (int q = 0; q < 4; q++) {
+      const float wxq = isX ? VX.wx[q] : VY.wx[q], dwxq = isX ? VX.dwx[q] : VY.dwx[q];
+      const float wyq = isX ? VX.wy[q] : VY.wy[q], dwyq = isX ? VX.dwy[q] : VY.dwy[q];
+      if (a == q) { wa = wxq; dwa = dwxq; }
+      if (b == q) { wb = wyq; dwb = dwyq; }
     }
-    const double Ra = (double)aX - (double)aY;
+    const int bxs = isX ? VX.bx : VY.bx, bys = isX ? VX.by : VY.by;
+    const float sv = img[(int64_t)clampi(bys - 1 + b, L.h) * L.w + clampi(bxs - 1 + a, L.w)];
+    float v = wa * wb * sv, vx = dwa * wb * sv, vy = wa * dwb * sv;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+      v += __shfl_xor_sync(kFull, v, o);
+      vx += __shfl_xor_sync(kFull, vx, o);
+      vy += __shfl_xor_sync(kFull, vy, o);
+    }
+    const float ov = __shfl_xor_sync(kFull, v, 16);
+    const float ovx = __shfl_xor_sync(kFull, vx, 16);
+    const float ovy = __shfl_xor_sync(kFull, vy, 16);
+    const float AX = (lane < 16) ? v : ov, AY = (lane < 16) ? ov : v;
+    aXx = (lane < 16) ? vx : ovx; aXy = (lane < 16) ? vy : ovy;
+    aYx = (lane < 16) ? ovx : vx; aYy = (lane < 16) ? ovy : vy;
+    const float Ra = AX - AY;
     if (ssd) {
       La = Ra * Ra;
-      dLa = 2.0 * Ra;
+      dLa = 2.0f * Ra;
     } else {
-      const double rr = Ra / (double)A.eps_h;
-      const double s = sqrt(1.0 + rr * rr);
-      dLa = rr / s;
-      La = (Ra * rr) / (1.0 + s);
+      const float rr = Ra * inv_eps;
+      const float qv = fmaf(rr, rr, 1.0f);
+      const float is = rsqrtf(qv);
+      dLa = rr * is;
+      La = __fdividef(Ra * rr, fmaf(qv, is, 1.0f));
     }
-    gAX[0] = aXx; gAX[1] = aXy; gAY[0] = aYx; gAY[1] = aYy;
   }
 
-  const double Lsum = acc[0];
-  A.str_out[p] = (1.0 - delta) * Lsum;
-  A.ang_out[p] = delta * d * La;
-  if (A.grad) {
-    const double eta = A.eta;
-    const double cs = eta * (1.0 - delta);
-    const double ca = delta * d / eta * dLa;
-    const double ddelta = -eta * Lsum + d * La / eta;
-    double* g = A.grad;
-    g[0 * nasc + p] = cs * acc[1] + ca * gAX[0];
-    g[1 * nasc + p] = cs * acc[2] + ca * gAX[1] + ddelta * delta0 * dvtx * vty;
-    g[2 * nasc + p] = cs * acc[3];
-    g[3 * nasc + p] = -cs * acc[4] - ca * gAY[0] + ddelta * delta0 * vtx * dvty;
-    g[4 * nasc + p] = -cs * acc[5] - ca * gAY[1];
-    g[5 * nasc + p] = -cs * acc[6];
+  // eight outputs of this A-scan, one per lane 0..7
+  const float eta = (float)A.eta;
+  const float Lsum = acc[0];
+  const float cs = eta * (1.0f - delta);
+  const float ca = delta * d / eta * dLa;
+  const float ddelta = -eta * Lsum + d * La / eta;
+  float out;
+  switch (lane) {
+    case 0: out = (1.0f - delta) * Lsum; break;
+    case 1: out = delta * d * La; break;
+    case 2: out = cs * acc[1] + ca * aXx; break;
+    case 3: out = cs * acc[2] + ca * aXy + ddelta * delta0 * dvtx * vty; break;
+    case 4: out = cs * acc[3]; break;
+    case 5: out = -cs * acc[4] - ca * aYx + ddelta * delta0 * vtx * dvty; break;
+    case 6: out = -cs * acc[5] - ca * aYy; break;
+    default: out = -cs * acc[6]; break;
   }
+  if (lane == 0) A.str_out[p] = out;
+  else if (lane == 1) A.ang_out[p] = out;
+  else if (lane < 8 && A.grad) A.grad[(int64_t)(lane - 2) * nasc + p] = out;
 }
 
 }  // namespace

@@ -73,16 +73,22 @@ __global__ void __launch_bounds__(kThreads) dots_kernel(const DotList L, int64_t
     if (t == kChunk && blockIdx.y == 0) partials[(int64_t)kMaxDots * G + blockIdx.x] = v;
   }
   if (last_block_2d(counter)) {
-    // the last block adds the partials of every dot in block order
-    for (int dd = threadIdx.x; dd <= L.n; dd += kThreads) {
+    // the last block adds the partials of each dot: one warp per dot, lanes
+    // take a fixed strided share of the blocks, then a butterfly
+    for (int dd = warp; dd <= L.n; dd += kThreads / 32) {
       const bool is_max = (dd == L.n);
       const int64_t row = is_max ? kMaxDots : dd;
       double v = 0.0;
-      for (int bx = 0; bx < G; bx++) {
+      for (int bx = lane; bx < G; bx += 32) {
         const double u = partials[row * G + bx];
         v = is_max ? fmax(v, u) : v + u;
       }
-      out[is_max ? kMaxDots : dd] = v;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = is_max ? fmax(v, u) : v + u;
+      }
+      if (lane == 0) out[is_max ? kMaxDots : dd] = v;
     }
     __syncthreads();
     if (threadIdx.x == 0) *counter = 0u;

@@ -5,85 +5,98 @@
 //                (the three sums of the mean term M).
 //   reg_kernel:  per A-scan, the temporal regulariser along each volume's
 //                acquisition chain (pairs n, n+1 weighted by omega_n,
-//                pseudo-Huber of the displacement difference), its gradient
-//                and dM/dD = 2 mu S_c are added to the data gradient; the
-//                block partial sums of S^str, S^ang, R and grad . dir are
-//                reduced by the last block in a fixed order:
-//                f = eta S^str + S^ang / eta + alpha R + mu sum_c S_c^2.
-// Both use a fixed grid and the "last block finishes" pattern: every block
-// writes its partials, the block that increments the counter last adds the
-// partials in block order and resets the counter.  No waits, no float
-// atomics, bitwise reproducible.
+//                pseudo-Huber of the displacement difference) and its
+//                gradient, plus dM/dD = 2 mu S_c, are added to the float
+//                data-term gradient and the sum is written as the float64
+//                gradient; the partial sums of S^str, S^ang, R and grad . dir
+//                are reduced to f = eta S^str + S^ang / eta + alpha R +
+//                mu sum_c S_c^2.
+//
+// Per-element arithmetic is float (double arithmetic is 1/64 of the float
+// rate on this GPU, with a long latency); each thread's float partials are
+// widened exactly and every sum across threads and blocks is a float64 tree
+// with a fixed shape.  The grid is fixed for a given size and the "last block
+// finishes" pattern adds the block partials: no waits, no float atomics,
+// bitwise reproducible.
 #include "common.cuh"
 
 namespace octmc {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kMsumBlocks = 304;   // 2 x 152 SMs
-constexpr int kMaxRegBlocks = 1216;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMsumBlocks = 152;
+constexpr int kMaxRegBlocks = 608;
 
+// Sum of v[c] over the block, result valid in thread 0 (fixed tree).
 template <int N>
-__device__ void block_sum(double (&v)[N], double* smem /* [N][kThreads/32] */) {
+__device__ void block_sum(double (&v)[N]) {
+  __shared__ double sm[N][kWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int c = 0; c < N; c++) {
-    double s = warp_sum(v[c]);
-    if (lane == 0) smem[c * (kThreads / 32) + warp] = s;
+    const double s = warp_sum(v[c]);
+    if (lane == 0) sm[c][warp] = s;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (warp == 0) {
 #pragma unroll
     for (int c = 0; c < N; c++) {
-      double s = 0.0;
-      for (int w = 0; w < kThreads / 32; w++) s += smem[c * (kThreads / 32) + w];
+      double s = lane < kWarps ? sm[c][lane] : 0.0;
+#pragma unroll
+      for (int o = kWarps / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       v[c] = s;
     }
   }
+  __syncthreads();
 }
 
-// Returns true in thread 0 of the last block to finish (partials visible).
+// True in every thread of the last block to finish (partials visible).
 __device__ bool last_block(unsigned* counter) {
   __shared__ bool is_last;
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned t = atomicAdd(counter, 1u);
-    is_last = (t == gridDim.x - 1);
-  }
+  if (threadIdx.x == 0) is_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
   __syncthreads();
-  if (is_last && threadIdx.x == 0) {
-    __threadfence();
-    return true;
-  }
-  return false;
+  if (is_last) __threadfence();
+  return is_last;
+}
+
+// The last block adds partials[b * N + c] over the blocks b, in a fixed
+// strided order per thread followed by block_sum.  Result in thread 0.
+template <int N>
+__device__ void sum_partials(const double* partials, int nblocks, double (&v)[N]) {
+#pragma unroll
+  for (int c = 0; c < N; c++) v[c] = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += kThreads)
+#pragma unroll
+    for (int c = 0; c < N; c++) v[c] += partials[b * N + c];
+  block_sum<N>(v);
 }
 
 __global__ void __launch_bounds__(kThreads) msum_kernel(const double* __restrict__ disp, int64_t plane,
                                                         EvalResult* res, double* partials,
                                                         unsigned* counter) {
-  __shared__ double sm[3 * (kThreads / 32)];
-  double v[3] = {0.0, 0.0, 0.0};
+  float f[3] = {0.f, 0.f, 0.f};
   for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < plane;
        e += (int64_t)gridDim.x * kThreads) {
 #pragma unroll
-    for (int c = 0; c < 3; c++) v[c] += disp[c * plane + e] + disp[(3 + c) * plane + e];
+    for (int c = 0; c < 3; c++) f[c] += narrow_trunc(disp[c * plane + e]) + narrow_trunc(disp[(3 + c) * plane + e]);
   }
-  block_sum<3>(v, sm);
+  double v[3] = {widen_exact(f[0]), widen_exact(f[1]), widen_exact(f[2])};
+  block_sum<3>(v);
   if (threadIdx.x == 0)
     for (int c = 0; c < 3; c++) partials[blockIdx.x * 3 + c] = v[c];
   if (last_block(counter)) {
-    for (int c = 0; c < 3; c++) {
-      double s = 0.0;
-      for (unsigned b = 0; b < gridDim.x; b++) s += partials[b * 3 + c];
-      res->msum[c] = s;
+    sum_partials<3>(partials, gridDim.x, v);
+    if (threadIdx.x == 0) {
+      for (int c = 0; c < 3; c++) res->msum[c] = v[c];
+      *counter = 0u;
     }
-    *counter = 0u;
   }
 }
 
-// Pseudo-Huber loss of a displacement difference (float: the differences
-// are O(1) px and the sums are taken in double).
+// Pseudo-Huber loss (and derivative) of a displacement difference.
 __device__ __forceinline__ float huber(float x, float inv_eps, float* dl) {
   const float r = x * inv_eps;
   const float q = fmaf(r, r, 1.0f);
@@ -93,65 +106,68 @@ __device__ __forceinline__ float huber(float x, float inv_eps, float* dl) {
 }
 
 __global__ void __launch_bounds__(kThreads) reg_kernel(const RegArgs A) {
-  __shared__ double sm[4 * (kThreads / 32)];
   const LevelDev& L = A.L;
   const int64_t n = (int64_t)L.w * L.h;
   const float inv_eps = (float)(1.0 / A.eps_r);
-  const double two_mu_s[3] = {2.0 * A.mu * A.result->msum[0], 2.0 * A.mu * A.result->msum[1],
-                              2.0 * A.mu * A.result->msum[2]};
+  const float alpha = (float)A.alpha;
+  float two_mu_s[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) two_mu_s[c] = (float)(2.0 * A.mu * A.result->msum[c]);
   double v[4] = {0.0, 0.0, 0.0, 0.0};  // S^str, S^ang, R, grad . dir
   for (int64_t p = (int64_t)blockIdx.x * kThreads + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * kThreads) {
-    v[0] += A.str_in[p];
-    v[1] += A.ang_in[p];
+    float r = 0.f, gd = 0.f;
 #pragma unroll
     for (int V = 0; V < 2; V++) {
       const int nx = L.next[V][p], pv = L.prev[V][p];
-      const double wn = nx >= 0 ? L.wnext[V][p] : 0.0;
-      const double wp = pv >= 0 ? L.wprev[V][p] : 0.0;
+      const float wn = nx >= 0 ? L.wnext[V][p] : 0.f;
+      const float wp = pv >= 0 ? L.wprev[V][p] : 0.f;
 #pragma unroll
       for (int c = 0; c < 3; c++) {
         const double* dc = A.disp + (V * 3 + c) * n;
-        const double x = dc[p];
-        double gr = 0.0;
+        const float x = narrow_trunc(dc[p]);
+        float gr = 0.f;
         if (nx >= 0) {  // pair (p, next) is counted at its first sample
           float dl;
-          const float lv = huber((float)(dc[nx] - x), inv_eps, &dl);
-          v[2] += wn * (double)lv;
-          gr -= wn * (double)dl;
+          r = fmaf(wn, huber(narrow_trunc(dc[nx]) - x, inv_eps, &dl), r);
+          gr = fmaf(-wn, dl, gr);
         }
         if (pv >= 0) {
           float dl;
-          huber((float)(x - dc[pv]), inv_eps, &dl);
-          gr += wp * (double)dl;
+          huber(x - narrow_trunc(dc[pv]), inv_eps, &dl);
+          gr = fmaf(wp, dl, gr);
         }
         if (A.grad) {
           const int64_t gi = (V * 3 + c) * n + p;
-          const double g = A.grad[gi] + A.alpha * gr + two_mu_s[c];
-          A.grad[gi] = g;
-          if (A.dir) v[3] += g * A.dir[gi];
+          const float g = A.gdata[gi] + fmaf(alpha, gr, two_mu_s[c]);
+          A.grad[gi] = widen_exact(g);
+          if (A.dir) gd = fmaf(g, narrow_trunc(A.dir[gi]), gd);
         }
       }
     }
+    v[0] += widen_exact(A.str_in[p]);
+    v[1] += widen_exact(A.ang_in[p]);
+    v[2] += widen_exact(r);
+    v[3] += widen_exact(gd);
   }
-  block_sum<4>(v, sm);
+  block_sum<4>(v);
   if (threadIdx.x == 0)
     for (int c = 0; c < 4; c++) A.partials[blockIdx.x * 4 + c] = v[c];
   if (last_block(A.counter)) {
-    double s[4] = {0.0, 0.0, 0.0, 0.0};
-    for (unsigned b = 0; b < gridDim.x; b++)
-      for (int c = 0; c < 4; c++) s[c] += A.partials[b * 4 + c];
-    const double* ms = A.result->msum;
-    const double M = A.mu * (ms[0] * ms[0] + ms[1] * ms[1] + ms[2] * ms[2]);
-    EvalResult* r = A.result;
-    r->terms[0] = s[0];
-    r->terms[1] = s[1];
-    r->terms[2] = s[2];
-    r->terms[3] = M;
-    r->terms[4] = A.eta * s[0] + s[1] / A.eta + A.alpha * s[2] + M;
-    r->terms[5] = A.eta;
-    r->gdir = s[3];
-    *A.counter = 0u;
+    sum_partials<4>(A.partials, gridDim.x, v);
+    if (threadIdx.x == 0) {
+      const double* ms = A.result->msum;
+      const double M = A.mu * (ms[0] * ms[0] + ms[1] * ms[1] + ms[2] * ms[2]);
+      EvalResult* res = A.result;
+      res->terms[0] = v[0];
+      res->terms[1] = v[1];
+      res->terms[2] = v[2];
+      res->terms[3] = M;
+      res->terms[4] = A.eta * v[0] + v[1] / A.eta + A.alpha * v[2] + M;
+      res->terms[5] = A.eta;
+      res->gdir = v[3];
+      *A.counter = 0u;
+    }
   }
 }
 
