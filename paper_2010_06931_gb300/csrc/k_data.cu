@@ -178,7 +178,7 @@ __device__ __forceinline__ void sample_block(const Vol& V, int kb, int lane, int
 }
 
 #ifndef OCTMC_DATA_MINB
-#define OCTMC_DATA_MINB 2
+#define OCTMC_DATA_MINB 3
 #endif
 __global__ void __launch_bounds__(kWarpsPerBlock * kWarp, OCTMC_DATA_MINB)
 data_kernel(const DataArgs A) {
