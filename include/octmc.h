@@ -45,6 +45,7 @@ extern "C" {
 #define OCTMC_ERR_NONFINITE (-4)
 #define OCTMC_ERR_TIMEOUT (-5)
 #define OCTMC_ERR_UNSUPPORTED (-6)
+#define OCTMC_ERR_SCRATCH_LIMIT (-7)
 
 typedef enum { OCTMC_F32 = 0, OCTMC_BF16 = 1, OCTMC_F16 = 2 } octmc_dtype;
 typedef enum { OCTMC_LOSS_PSEUDO_HUBER = 0, OCTMC_LOSS_SSD = 1 } octmc_loss;
@@ -174,6 +175,34 @@ int octmc_lbfgs_reset(octmc_lbfgs *h);
 int octmc_profile_enable(octmc_problem *p, int enable);
 /* Total milliseconds and number of timed data-term launches so far. */
 int octmc_profile_read(octmc_problem *p, double *total_ms, long long *launches);
+
+/* ---------------------------------------------------------------------
+ * Data term without any allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc (code inside a
+ * memory-pool or allocator callback, frameworks that own all device memory,
+ * paths where allocating after start-up is forbidden).  It evaluates
+ * S^str = sum (1 - delta) sum_k L(R_ijk) and S^ang = sum delta d L(R_ij(A))
+ * (Eq. 5, 6) of one grid and eta*S^str + S^ang/eta's gradient with respect
+ * to the displacements, using the same kernel as the other entry points.
+ *   sx, sy: device float32 [h][w][d] with d a multiple of 4 (>= 4);
+ *   ax, ay: device [h][w] or both NULL; vx[h], vy[w]: device or NULL;
+ *   disp: device float64 [2][3][h][w];
+ *   grad_out: device float64 [2][3][h][w] or NULL (data-term gradient);
+ *   sums_out: device float64 [2] receives S^str, S^ang.
+ * Its scratch is one file-scope device array of 8 MiB (+2.4 KiB), held by
+ * every GPU that loads the library until the process exits; it fits grids
+ * of at most 262,144 A-scans (w*h); larger grids return
+ * OCTMC_ERR_SCRATCH_LIMIT.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  Every call shares the array and
+ * leaves its contents behind: calls that overlap on the GPU (other streams,
+ * other threads, same device) race and give wrong results.  Asynchronous on
+ * `stream`; errors: INVALID_ARG, SCRATCH_LIMIT, CUDA.
+ * --------------------------------------------------------------------- */
+int octmc_data_term_static(const float *sx, const float *sy, const float *ax, const float *ay,
+                           const float *vx, const float *vy, int w, int h, int d, const double *disp,
+                           double eta, double delta0, double eps_h, int loss, double *grad_out,
+                           double *sums_out, void *stream);
 
 /* Human-readable name of a return code. */
 const char *octmc_status_string(int code);

@@ -8,7 +8,8 @@ LIB_PATH = os.path.join(_HERE, "liboctmc.so")
 OK = 0
 NOT_CONVERGED = 1
 ERRORS = {-1: "invalid argument", -2: "out of device memory", -3: "CUDA error",
-          -4: "objective is not finite", -5: "device wait timed out", -6: "unsupported"}
+          -4: "objective is not finite", -5: "device wait timed out", -6: "unsupported",
+          -7: "grid exceeds the static scratch"}
 
 F32, BF16, F16 = 0, 1, 2
 LOSS_PSEUDO_HUBER, LOSS_SSD = 0, 1
@@ -59,6 +60,8 @@ _SIGS = {
     "octmc_lbfgs_reset": (C.c_int, [C.c_void_p]),
     "octmc_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "octmc_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
+    "octmc_data_term_static": (C.c_int, [C.c_void_p] * 6 + [C.c_int] * 3 + [C.c_void_p] + [C.c_double] * 3
+                               + [C.c_int] + [C.c_void_p] * 3),
     "octmc_status_string": (C.c_char_p, [C.c_int]),
 }
 

@@ -895,6 +895,7 @@ const char* octmc_status_string(int code) {
     case OCTMC_ERR_NONFINITE: return "objective is not finite";
     case OCTMC_ERR_TIMEOUT: return "device wait timed out";
     case OCTMC_ERR_UNSUPPORTED: return "unsupported (needs an sm_103a device / dtype not built)";
+    case OCTMC_ERR_SCRATCH_LIMIT: return "grid larger than the static scratch of octmc_data_term_static";
     default: return "unknown status";
   }
 }
