@@ -314,6 +314,7 @@ struct octmc_problem {
   double* gb = nullptr;
   double* dir = nullptr;
   octmc_lbfgs* opt = nullptr;
+  std::vector<void*> temps;  // float32 pyramid copies while building 16-bit storage
   // optional CUDA-event timing of the data-term kernel (octmc_profile_*)
   bool profile = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -322,6 +323,7 @@ struct octmc_problem {
   bool prof_pending = false;
 
   ~octmc_problem() {
+    for (void* t : temps) dfree(t);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
     for (Level& L : lv) {
@@ -392,15 +394,24 @@ void create_impl(octmc_problem* P) {
   const octmc_desc& D = P->desc;
   check_device();
   const int L = D.levels;
+  const int dt = D.storage;
   P->lv.resize(L);
   int w = D.w, h = D.h, d = D.d;
   std::vector<double> tx = fetch_times(P, D.tx, (size_t)w * h), ty = fetch_times(P, D.ty, (size_t)w * h);
+  // The pyramid is built in float32; with 16-bit storage every level is
+  // rounded once (to nearest even) from its float32 box means, and the
+  // float32 copies are temporaries (kept in P->temps until released).
+  float* prev32[2] = {nullptr, nullptr};
   for (int l = 0; l < L; l++) {
     LevelDev& X = P->lv[l].dev;
     X.w = w; X.h = h; X.d = d; X.dp = pad4(d);
+    X.dtype = dt;
     const int64_t cols = (int64_t)w * h;
-    X.sx = dalloc<float>((size_t)cols * X.dp);
-    X.sy = dalloc<float>((size_t)cols * X.dp);
+    float* cur32[2];
+    for (int V = 0; V < 2; V++) {
+      cur32[V] = dalloc<float>((size_t)cols * X.dp);
+      if (dt != OCTMC_F32) P->temps.push_back(cur32[V]);
+    }
     if (P->have_ang) {
       X.ax = dalloc<float>((size_t)cols);
       X.ay = dalloc<float>((size_t)cols);
@@ -408,8 +419,8 @@ void create_impl(octmc_problem* P) {
     if (D.vx) X.vx = dalloc<float>((size_t)h);
     if (D.vy) X.vy = dalloc<float>((size_t)w);
     if (l == 0) {
-      upload_volume(P, D.sx, X.sx, w, h, d, X.dp);
-      upload_volume(P, D.sy, X.sy, w, h, d, X.dp);
+      upload_volume(P, D.sx, cur32[0], w, h, d, X.dp);
+      upload_volume(P, D.sy, cur32[1], w, h, d, X.dp);
       if (P->have_ang) {
         upload(P, D.ax, X.ax, (size_t)cols);
         upload(P, D.ay, X.ay, (size_t)cols);
@@ -418,8 +429,8 @@ void create_impl(octmc_problem* P) {
       if (D.vy) upload(P, D.vy, X.vy, (size_t)w);
     } else {
       const LevelDev& F = P->lv[l - 1].dev;
-      CK(launch_pyr_volume(F.sx, F.w, F.h, F.d, F.dp, X.sx, w, h, d, X.dp, P->st));
-      CK(launch_pyr_volume(F.sy, F.w, F.h, F.d, F.dp, X.sy, w, h, d, X.dp, P->st));
+      for (int V = 0; V < 2; V++)
+        CK(launch_pyr_volume(prev32[V], F.w, F.h, F.d, F.dp, cur32[V], w, h, d, X.dp, P->st));
       if (P->have_ang) {
         CK(launch_pyr_image(F.ax, F.w, F.h, X.ax, P->st));
         CK(launch_pyr_image(F.ay, F.w, F.h, X.ay, P->st));
@@ -429,6 +440,17 @@ void create_impl(octmc_problem* P) {
       tx = time_down(tx, F.w, F.h);
       ty = time_down(ty, F.w, F.h);
     }
+    if (dt == OCTMC_F32) {
+      X.sx = cur32[0];
+      X.sy = cur32[1];
+    } else {
+      X.sx = dalloc<uint16_t>((size_t)cols * X.dp);
+      X.sy = dalloc<uint16_t>((size_t)cols * X.dp);
+      CK(launch_convert(cur32[0], X.sx, dt, cols * X.dp, P->st));
+      CK(launch_convert(cur32[1], X.sy, dt, cols * X.dp, P->st));
+    }
+    prev32[0] = cur32[0];
+    prev32[1] = cur32[1];
     for (int V = 0; V < 2; V++) {
       std::vector<int> pv, nx;
       std::vector<float> wp, wn;
@@ -458,6 +480,8 @@ void create_impl(octmc_problem* P) {
   P->res = dalloc<EvalResult>(1);
   CK(cudaMallocHost(&P->res_host, sizeof(EvalResult)));
   CK(cudaStreamSynchronize(P->st));
+  for (void* t : P->temps) dfree(t);
+  P->temps.clear();
 }
 
 void collect_profile(octmc_problem* P) {
@@ -684,10 +708,7 @@ int octmc_create_problem(const octmc_desc* desc, octmc_problem** out) {
   if (D.loss != OCTMC_LOSS_PSEUDO_HUBER && D.loss != OCTMC_LOSS_SSD) return OCTMC_ERR_INVALID_ARG;
   if (!(D.eps_h > 0) || !(D.eps_r > 0) || !(D.alpha >= 0) || !(D.delta0 >= 0)) return OCTMC_ERR_INVALID_ARG;
   if ((int64_t)D.w * D.h * pad4(D.d) / 4 >= (int64_t)1 << 32) return OCTMC_ERR_INVALID_ARG;
-  if (D.storage != OCTMC_F32) {
-    if (D.storage == OCTMC_BF16 || D.storage == OCTMC_F16) return OCTMC_ERR_UNSUPPORTED;
-    return OCTMC_ERR_INVALID_ARG;
-  }
+  if (D.storage != OCTMC_F32 && D.storage != OCTMC_BF16 && D.storage != OCTMC_F16) return OCTMC_ERR_INVALID_ARG;
   octmc_problem* P = new (std::nothrow) octmc_problem();
   if (!P) return OCTMC_ERR_OOM;
   P->desc = D;
@@ -802,8 +823,8 @@ int octmc_level_data(const octmc_problem* p, int level, float* sx, float* sy, fl
   return guarded([&] {
     const LevelDev& L = q->lv[level].dev;
     const int64_t cols = (int64_t)L.w * L.h;
-    if (sx) CK(launch_unpad_depth(L.sx, cols, L.d, L.dp, sx, q->st));
-    if (sy) CK(launch_unpad_depth(L.sy, cols, L.d, L.dp, sy, q->st));
+    if (sx) CK(launch_unpad_depth(L.sx, L.dtype, cols, L.d, L.dp, sx, q->st));
+    if (sy) CK(launch_unpad_depth(L.sy, L.dtype, cols, L.d, L.dp, sy, q->st));
     if (ax && L.ax) CK(cudaMemcpyAsync(ax, L.ax, sizeof(float) * cols, cudaMemcpyDeviceToDevice, q->st));
     if (ay && L.ay) CK(cudaMemcpyAsync(ay, L.ay, sizeof(float) * cols, cudaMemcpyDeviceToDevice, q->st));
     if (vx && L.vx) CK(cudaMemcpyAsync(vx, L.vx, sizeof(float) * L.h, cudaMemcpyDeviceToDevice, q->st));

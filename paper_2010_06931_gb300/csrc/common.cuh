@@ -152,8 +152,9 @@ __device__ __forceinline__ double warp_sum(double v) {
 // so aligned 4-sample groups inside [0, dp) read clamp-to-edge values.
 struct LevelDev {
   int w, h, d, dp;
-  float* sx;
-  float* sy;
+  int dtype;  // octmc_dtype of sx, sy (float32, bfloat16 or float16 samples)
+  void* sx;
+  void* sy;
   float* ax;  // [h][w] or null
   float* ay;
   float* vx;  // [h] or null
@@ -216,8 +217,9 @@ cudaError_t launch_pyr_image(const float* in, int w, int h, float* out, cudaStre
 cudaError_t launch_pyr_line(const float* in, int n, float* out, cudaStream_t s);
 cudaError_t launch_prolong(const double* coarse, int wc, int hc, double* fine, int wf, int hf,
                            cudaStream_t s);
-cudaError_t launch_unpad_depth(const float* vol, int64_t columns, int d, int dp, float* out,
+cudaError_t launch_unpad_depth(const void* vol, int dtype, int64_t columns, int d, int dp, float* out,
                                cudaStream_t s);
+cudaError_t launch_convert(const float* in, void* out, int dtype, int64_t n, cudaStream_t s);
 
 // L-BFGS vector kernels (float64).
 constexpr int kMaxDots = 80;

@@ -19,6 +19,9 @@
 // input depths the 4-tap axial filter needs from the adjacent lanes by
 // shuffles.  Lanes 0, 30 and 31 only supply those halo values.  Per-A-scan
 // sums are reduced with a fixed butterfly, so results are deterministic.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 
 namespace octmc {
@@ -30,7 +33,7 @@ constexpr int kOutPerIter = 4 * kOutLanes;
 constexpr unsigned kFull = 0xffffffffu;
 
 struct Vol {
-  const float4* base;  // the volume as 4-sample groups
+  const void* base;    // the volume; addressed in groups of 4 samples
   unsigned roff[4];    // row offsets (in groups) of the 4 neighbour rows
   unsigned coff[4];    // column offsets (in groups) of the 4 neighbour columns
   float wx[4], dwx[4], wy[4], dwy[4], wz[4], dwz[4];
@@ -63,7 +66,7 @@ __device__ __forceinline__ void split_displacement(const double* disp, int64_t n
   }
 }
 
-__device__ __forceinline__ void setup_vol(Vol& V, const float* vol, const LevelDev& L, const int base[3],
+__device__ __forceinline__ void setup_vol(Vol& V, const void* vol, const LevelDev& L, const int base[3],
                                           const float frac[3]) {
   V.bx = base[0];
   V.by = base[1];
@@ -79,7 +82,29 @@ __device__ __forceinline__ void setup_vol(Vol& V, const float* vol, const LevelD
     V.roff[a] = (unsigned)clampi(V.by - 1 + a, L.h) * (unsigned)L.w * nq;
     V.coff[a] = (unsigned)clampi(V.bx - 1 + a, L.w) * nq;
   }
-  V.base = reinterpret_cast<const float4*>(vol);
+  V.base = vol;
+}
+
+// Four consecutive samples (one aligned group) widened to float: float32
+// storage is one 16-byte load, bfloat16/float16 one 8-byte load.
+template <typename T>
+__device__ __forceinline__ float4 load4(const void* base, unsigned idx);
+template <>
+__device__ __forceinline__ float4 load4<float>(const void* base, unsigned idx) {
+  return __ldg(reinterpret_cast<const float4*>(base) + idx);
+}
+template <>
+__device__ __forceinline__ float4 load4<__nv_bfloat16>(const void* base, unsigned idx) {
+  const uint2 u = __ldg(reinterpret_cast<const uint2*>(base) + idx);
+  return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                     __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+}
+template <>
+__device__ __forceinline__ float4 load4<__half>(const void* base, unsigned idx) {
+  const uint2 u = __ldg(reinterpret_cast<const uint2*>(base) + idx);
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+  return make_float4(a.x, a.y, b.x, b.y);
 }
 
 __device__ __forceinline__ void fma4(float4& acc, float w, const float4& s) {
@@ -145,6 +170,7 @@ __device__ __forceinline__ void axial(const float4& T, const float4& Tx, const f
 
 // Interpolated values (and their displacement derivatives) of one volume
 // at the lane's 4 outputs of the depth block starting at kb.
+template <typename S>
 __device__ __forceinline__ void sample_block(const Vol& V, int kb, int lane, int dp, float I[4],
                                              float Iz[4], float Ix[4], float Iy[4]) {
   const int qk = kb + 4 * V.q + 4 * (lane - 1);  // first input depth of the lane's group
@@ -155,7 +181,7 @@ __device__ __forceinline__ void sample_block(const Vol& V, int kb, int lane, int
     float4 U = bcast(0.f), Ux = bcast(0.f);
 #pragma unroll
     for (int a = 0; a < 4; a++) {
-      const float4 s = __ldg(V.base + (V.roff[b] + V.coff[a] + qc));
+      const float4 s = load4<S>(V.base, V.roff[b] + V.coff[a] + qc);
       fma4(U, V.wx[a], s);
       fma4(Ux, V.dwx[a], s);
     }
@@ -180,6 +206,7 @@ __device__ __forceinline__ void sample_block(const Vol& V, int kb, int lane, int
 #ifndef OCTMC_DATA_MINB
 #define OCTMC_DATA_MINB 3
 #endif
+template <typename T>
 __global__ void __launch_bounds__(kWarpsPerBlock * kWarp, OCTMC_DATA_MINB)
 data_kernel(const DataArgs A) {
   const LevelDev& L = A.L;
@@ -201,8 +228,8 @@ data_kernel(const DataArgs A) {
   float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   for (int kb = 0; kb < L.d; kb += kOutPerIter) {
     float IX[4], IzX[4], IxX[4], IyX[4], IY[4], IzY[4], IxY[4], IyY[4];
-    sample_block(VX, kb, lane, L.dp, IX, IzX, IxX, IyX);
-    sample_block(VY, kb, lane, L.dp, IY, IzY, IxY, IyY);
+    sample_block<T>(VX, kb, lane, L.dp, IX, IzX, IxX, IyX);
+    sample_block<T>(VY, kb, lane, L.dp, IY, IzY, IxY, IyY);
     if (lane >= 1 && lane <= kOutLanes) {
 #pragma unroll
       for (int o = 0; o < 4; o++) {
@@ -330,7 +357,12 @@ cudaError_t launch_data(const DataArgs& a, cudaStream_t s) {
   const int64_t nasc = (int64_t)a.L.w * a.L.h;
   const int64_t blocks = (nasc + kWarpsPerBlock - 1) / kWarpsPerBlock;
   if (blocks <= 0) return cudaSuccess;
-  data_kernel<<<(unsigned)blocks, kWarpsPerBlock * kWarp, 0, s>>>(a);
+  if (a.L.dtype == OCTMC_BF16)
+    data_kernel<__nv_bfloat16><<<(unsigned)blocks, kWarpsPerBlock * kWarp, 0, s>>>(a);
+  else if (a.L.dtype == OCTMC_F16)
+    data_kernel<__half><<<(unsigned)blocks, kWarpsPerBlock * kWarp, 0, s>>>(a);
+  else
+    data_kernel<float><<<(unsigned)blocks, kWarpsPerBlock * kWarp, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -6,6 +6,9 @@
 // sample repeats the edge sample.  The 8 (4, 2) float samples are added in
 // double, which is exact for float inputs of similar magnitude, and the mean
 // is rounded once to float.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 
 namespace octmc {
@@ -24,13 +27,30 @@ __global__ void pad_depth_kernel(float* vol, int64_t columns, int d, int dp) {
   }
 }
 
-__global__ void unpad_depth_kernel(const float* vol, int64_t columns, int d, int dp, float* out) {
+__device__ __forceinline__ float to_float(float v) { return v; }
+__device__ __forceinline__ float to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_float(__half v) { return __half2float(v); }
+
+template <typename T>
+__global__ void unpad_depth_kernel(const T* vol, int64_t columns, int d, int dp, float* out) {
   const int64_t n = columns * d;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t col = e / d;
-    out[e] = vol[col * dp + (e % d)];
+    out[e] = to_float(vol[col * dp + (e % d)]);
   }
+}
+
+// float32 -> storage type, round to nearest even.
+__device__ __forceinline__ void store_as(float* p, float v) { *p = v; }
+__device__ __forceinline__ void store_as(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+__device__ __forceinline__ void store_as(__half* p, float v) { *p = __float2half_rn(v); }
+
+template <typename T>
+__global__ void convert_kernel(const float* __restrict__ in, T* __restrict__ out, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    store_as(out + e, in[e]);
 }
 
 // One thread per output sample (i2, j2, k2) including the depth pad.
@@ -116,9 +136,26 @@ cudaError_t launch_pad_depth(float* vol, int64_t columns, int d, int dp, cudaStr
   return cudaGetLastError();
 }
 
-cudaError_t launch_unpad_depth(const float* vol, int64_t columns, int d, int dp, float* out,
+cudaError_t launch_unpad_depth(const void* vol, int dtype, int64_t columns, int d, int dp, float* out,
                                cudaStream_t s) {
-  unpad_depth_kernel<<<grid_for(columns * d), kThreads, 0, s>>>(vol, columns, d, dp, out);
+  const unsigned g = grid_for(columns * d);
+  if (dtype == OCTMC_BF16)
+    unpad_depth_kernel<<<g, kThreads, 0, s>>>(static_cast<const __nv_bfloat16*>(vol), columns, d, dp, out);
+  else if (dtype == OCTMC_F16)
+    unpad_depth_kernel<<<g, kThreads, 0, s>>>(static_cast<const __half*>(vol), columns, d, dp, out);
+  else
+    unpad_depth_kernel<<<g, kThreads, 0, s>>>(static_cast<const float*>(vol), columns, d, dp, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(const float* in, void* out, int dtype, int64_t n, cudaStream_t s) {
+  const unsigned g = grid_for(n);
+  if (dtype == OCTMC_BF16)
+    convert_kernel<<<g, kThreads, 0, s>>>(in, static_cast<__nv_bfloat16*>(out), n);
+  else if (dtype == OCTMC_F16)
+    convert_kernel<<<g, kThreads, 0, s>>>(in, static_cast<__half*>(out), n);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

@@ -1,0 +1,85 @@
+"""16-bit volume storage (GPU).
+
+With bfloat16 or float16 storage every pyramid level is the float32 box
+mean rounded once to nearest even; interpolation and accumulation stay in
+float32.  The kernel result is compared with the FP64 oracle run on the same
+rounded values (kernel error), and the rounding error itself is measured
+against the oracle on the float32 originals (reported, loosely bounded).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from octsynth import make_config, make_pair, true_displacement
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def round_bf16(a):
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32)
+
+
+def round_f16(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float16).astype(np.float32)
+
+
+ROUND = {1: round_bf16, 2: round_f16}
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+def test_pyramid_levels_are_rounded_box_means(storage):
+    import paper_2010_06931_gb300 as octmc
+    p = make_pair(37, 29, 51, n_layers=4, n_slabs=1, n_saccades=1, max_saccade=2.0, drift_sigma=0.05, seed=8)
+    G = octmc.Problem(p["sx"], p["sy"], p["tx"], p["ty"], p["ax"], p["ay"], p["vx"], p["vy"],
+                      levels=3, storage=storage)
+    C = O.OracleProblem(p["sx"], p["sy"], p["tx"], p["ty"], p["ax"], p["ay"], p["vx"], p["vy"]).pyramid(3)
+    for l in range(3):
+        got = G.level_data(l)
+        for k in ("sx", "sy"):
+            assert np.array_equal(got[k].cpu().numpy(), ROUND[storage](getattr(C[l], k))), (l, k)
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+def test_eval_parity_on_rounded_volumes(storage):
+    import paper_2010_06931_gb300 as octmc
+    p, cfg = make_config("c1")
+    T, _ = true_displacement(p, cfg["w"], cfg["h"])
+    D = T + np.random.default_rng(1).normal(0.0, 0.3, T.shape)
+    G = octmc.Problem(p["sx"], p["sy"], p["tx"], p["ty"], p["ax"], p["ay"], p["vx"], p["vy"], storage=storage)
+    rs, ry = ROUND[storage](p["sx"]), ROUND[storage](p["sy"])
+    Cr = O.OracleProblem(rs, ry, p["tx"], p["ty"], p["ax"], p["ay"], p["vx"], p["vy"])
+    C = O.OracleProblem(p["sx"], p["sy"], p["tx"], p["ty"], p["ax"], p["ay"], p["vx"], p["vy"])
+    G.set_eta(0, 0.8)
+    Cr.eta = C.eta = 0.8
+    g = torch.empty((2, 3, cfg["h"], cfg["w"]), dtype=torch.float64, device="cuda")
+    t = G.eval_terms(0, torch.from_numpy(D).cuda(), g)
+    fr, gr, _ = Cr.eval(D)
+    f0, g0, _ = C.eval(D)
+    gn = g.cpu().numpy()
+    # kernel error: same (rounded) data on both sides
+    assert abs(t[4] - fr) <= 1e-5 * abs(fr)
+    assert np.linalg.norm(gn - gr) <= 1e-4 * np.linalg.norm(gr)
+    # storage error against the float32 originals, reported and loosely bounded
+    ef = abs(t[4] - f0) / abs(f0)
+    eg = np.linalg.norm(gn - g0) / np.linalg.norm(g0)
+    print("storage %d: f rel err vs FP64 on float32 inputs %.2e, grad rel L2 %.2e" % (storage, ef, eg))
+    assert ef < 2e-2 and eg < 0.2
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+def test_solve_with_16bit_storage_tracks_float32(storage):
+    # same start, same algorithm: the 16-bit solution stays close to the float32 one
+    import paper_2010_06931_gb300 as octmc
+    p, cfg = make_config("c1")
+    kw = dict(alpha=1.0, loss=1, max_iter=150)
+    G32 = octmc.Problem(p["sx"], p["sy"], p["tx"], p["ty"], p["ax"], p["ay"], p["vx"], p["vy"], **kw)
+    G16 = octmc.Problem(p["sx"], p["sy"], p["tx"], p["ty"], p["ax"], p["ay"], p["vx"], p["vy"], storage=storage, **kw)
+    D32, D16 = G32.zeros(0), G16.zeros(0)
+    G32.solve_level(0, D32)
+    G16.solve_level(0, D16)
+    rms = float(torch.sqrt(((D32 - D16) ** 2).mean()))
+    print("storage %d: solution RMS vs float32 storage %.4f px" % (storage, rms))
+    assert rms < 0.25
