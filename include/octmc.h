@@ -167,6 +167,57 @@ int octmc_lbfgs_direction(octmc_lbfgs *h, const double *g_dev, double *dir_dev, 
 int octmc_lbfgs_reset(octmc_lbfgs *h);
 
 /* ---------------------------------------------------------------------
+ * Serving: continuous batching of independent full solves (Sec. 2.1 per
+ * request).  Requests wait in a FIFO queue and are admitted while a slot is
+ * free and their estimated device memory (octmc_estimate_bytes) fits the
+ * budget; once admitted their problem lives on the device.  Each
+ * octmc_server_step runs ONE batched objective evaluation for every admitted
+ * request (each at its own pyramid level, iteration and line-search trial;
+ * one launch per kernel for all of them) and then each request's L-BFGS
+ * bookkeeping.  A request's result does not depend on the other requests in
+ * the batch: its kernels use the same partition and reduction order as a
+ * solve of it alone (octmc_solve_full).  All work is on the server's stream.
+ * --------------------------------------------------------------------- */
+typedef struct octmc_server octmc_server;
+
+#define OCTMC_REQ_UNKNOWN (-1)
+#define OCTMC_REQ_QUEUED 0
+#define OCTMC_REQ_RUNNING 1
+#define OCTMC_REQ_DONE 2
+
+/* Device bytes a problem with this description needs while it is solved
+ * (volumes of every level, 16-bit conversion temporaries, workspace, L-BFGS
+ * history, result); -1 for an invalid size. */
+int64_t octmc_estimate_bytes(const octmc_desc *desc);
+
+/* budget_bytes: device memory the admitted requests may use together;
+ * max_slots: requests solved together at most; stream: cudaStream_t. */
+int octmc_server_create(int64_t budget_bytes, int max_slots, void *stream, octmc_server **out);
+void octmc_server_destroy(octmc_server *s);
+
+/* Queues a full solve of `desc` (its stream field is ignored).  The arrays
+ * the description points to must stay valid until the request has been
+ * admitted (state RUNNING or DONE).  *ticket identifies the request.
+ * Errors: INVALID_ARG; OOM if the request can never fit the budget. */
+int octmc_server_submit(octmc_server *s, const octmc_desc *desc, int64_t *ticket);
+
+/* Admits what fits, then one batched evaluation step for all admitted
+ * requests.  *active / *queued (may be NULL) receive the counts after the
+ * step.  A request whose admission fails is DONE with its error code. */
+int octmc_server_step(octmc_server *s, int *active, int *queued);
+
+/* *state = OCTMC_REQ_* of the request; nothing else happens. */
+int octmc_server_state(const octmc_server *s, int64_t ticket, int *state);
+
+/* *state = OCTMC_REQ_*.  When DONE: the level-0 displacement field is copied
+ * to disp_out_dev (device, 6*w*h float64, may be NULL), up to max_stats
+ * per-level statistics (coarse to fine) to stats, the request's return code
+ * to *req_rc, and the request's memory is released (the ticket is then
+ * unknown). */
+int octmc_server_poll(octmc_server *s, int64_t ticket, int *state, double *disp_out_dev, octmc_stats *stats,
+                      int max_stats, int *req_rc);
+
+/* ---------------------------------------------------------------------
  * Kernel timing: when enabled, every evaluation records CUDA events on the
  * problem's stream around the data-term kernel (resampling, loss and
  * per-A-scan gradient) and adds the elapsed time once the evaluation has

@@ -20,8 +20,8 @@ import torch
 from . import _native as N
 from ._native import BF16, F16, F32, LOSS_PSEUDO_HUBER, LOSS_SSD, OctmcError  # noqa: F401
 
-__all__ = ["Problem", "Lbfgs", "create_problem", "OctmcError", "F32", "BF16", "F16",
-           "LOSS_PSEUDO_HUBER", "LOSS_SSD", "library_path"]
+__all__ = ["Problem", "Lbfgs", "Server", "create_problem", "estimate_bytes", "OctmcError", "F32", "BF16",
+           "F16", "LOSS_PSEUDO_HUBER", "LOSS_SSD", "library_path"]
 
 
 def library_path():
@@ -226,3 +226,97 @@ class Lbfgs:
             self.destroy()
         except Exception:
             pass
+
+
+class Server:
+    """Continuous-batching solver (``octmc_server_*``).
+
+    ``submit`` queues a full coarse-to-fine solve of one scan pair and returns
+    a ticket; ``step`` admits what fits the device-memory budget and runs one
+    batched evaluation step for every admitted request; ``poll`` returns the
+    result of a finished request (and releases it).
+    """
+
+    QUEUED, RUNNING, DONE, UNKNOWN = 0, 1, 2, -1
+
+    def __init__(self, budget_bytes, max_slots=32):
+        self._h = C.c_void_p()
+        N.check(N.lib().octmc_server_create(int(budget_bytes), int(max_slots), _stream_ptr(), C.byref(self._h)),
+                "octmc_server_create")
+        self._inputs = {}  # ticket -> (tensors kept alive until admission, levels, shape)
+
+    def submit(self, sx, sy, tx, ty, ax=None, ay=None, vx=None, vy=None, *, storage=F32, alpha=0.1,
+               delta0=0.5, eps_h=1e-3, eps_r=1e-2, mu=0.0, loss=LOSS_PSEUDO_HUBER, levels=1, lbfgs_m=8,
+               max_iter=200, max_ls=20, gtol=1e-6, ftol=1e-9):
+        arrays = [sx, sy, tx, ty, ax, ay, vx, vy]
+        on_dev = all(isinstance(a, torch.Tensor) and a.is_cuda for a in arrays if a is not None)
+        dev = torch.device("cuda") if on_dev else torch.device("cpu")
+        f32 = lambda a: _as_tensor(a, torch.float32, dev)
+        f64 = lambda a: _as_tensor(a, torch.float64, dev)
+        keep = dict(sx=f32(sx), sy=f32(sy), tx=f64(tx), ty=f64(ty), ax=f32(ax), ay=f32(ay), vx=f32(vx), vy=f32(vy))
+        h, w, d = keep["sx"].shape
+        desc = N.Desc()
+        N.lib().octmc_desc_defaults(C.byref(desc))
+        desc.w, desc.h, desc.d, desc.storage = w, h, d, storage
+        for name in ("sx", "sy", "ax", "ay", "vx", "vy", "tx", "ty"):
+            setattr(desc, name, None if keep[name] is None else keep[name].data_ptr())
+        desc.inputs_on_device = 1 if on_dev else 0
+        desc.alpha, desc.delta0, desc.eps_h, desc.eps_r, desc.mu = alpha, delta0, eps_h, eps_r, mu
+        desc.loss, desc.levels, desc.lbfgs_m = loss, levels, lbfgs_m
+        desc.max_iter, desc.max_ls, desc.gtol, desc.ftol = max_iter, max_ls, gtol, ftol
+        t = C.c_int64()
+        N.check(N.lib().octmc_server_submit(self._h, C.byref(desc), C.byref(t)), "octmc_server_submit")
+        self._inputs[t.value] = (keep, levels, (h, w))
+        return t.value
+
+    def step(self):
+        a, q = C.c_int(), C.c_int()
+        N.check(N.lib().octmc_server_step(self._h, C.byref(a), C.byref(q)), "octmc_server_step")
+        # inputs of admitted requests are no longer needed
+        return a.value, q.value
+
+    def state(self, ticket):
+        st = C.c_int()
+        N.check(N.lib().octmc_server_state(self._h, int(ticket), C.byref(st)), "octmc_server_state")
+        return st.value
+
+    def poll(self, ticket):
+        """(state, field or None, stats or None, return code or None).  A finished
+        request is released by this call."""
+        if self.state(ticket) != self.DONE:
+            return self.state(ticket), None, None, None
+        keep, levels, (h, w) = self._inputs.get(ticket, (None, 1, (0, 0)))
+        state = C.c_int()
+        if keep is None:
+            N.check(N.lib().octmc_server_poll(self._h, int(ticket), C.byref(state), None, None, 0, None),
+                    "octmc_server_poll")
+            return state.value, None, None, None
+        # poll releases a finished request, so the result buffer goes with it
+        out = torch.empty((2, 3, h, w), dtype=torch.float64, device="cuda")
+        st = (N.Stats * levels)()
+        rc = C.c_int()
+        N.check(N.lib().octmc_server_poll(self._h, int(ticket), C.byref(state), _ptr(out), st, levels, C.byref(rc)),
+                "octmc_server_poll")
+        if state.value != self.DONE:
+            return state.value, None, None, None
+        del self._inputs[ticket]
+        return state.value, out, [s.as_dict() for s in st], rc.value
+
+    def destroy(self):
+        if self._h:
+            N.lib().octmc_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def estimate_bytes(w, h, d, levels=1, storage=F32, lbfgs_m=8):
+    """``octmc_estimate_bytes`` for a problem of this size."""
+    desc = N.Desc()
+    N.lib().octmc_desc_defaults(C.byref(desc))
+    desc.w, desc.h, desc.d, desc.levels, desc.storage, desc.lbfgs_m = w, h, d, levels, storage, lbfgs_m
+    return int(N.lib().octmc_estimate_bytes(C.byref(desc)))

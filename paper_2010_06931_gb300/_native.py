@@ -62,6 +62,14 @@ _SIGS = {
     "octmc_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "octmc_data_term_static": (C.c_int, [C.c_void_p] * 6 + [C.c_int] * 3 + [C.c_void_p] + [C.c_double] * 3
                                + [C.c_int] + [C.c_void_p] * 3),
+    "octmc_estimate_bytes": (C.c_int64, [C.POINTER(Desc)]),
+    "octmc_server_create": (C.c_int, [C.c_int64, C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "octmc_server_destroy": (None, [C.c_void_p]),
+    "octmc_server_submit": (C.c_int, [C.c_void_p, C.POINTER(Desc), C.POINTER(C.c_int64)]),
+    "octmc_server_step": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "octmc_server_state": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_int)]),
+    "octmc_server_poll": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_int), C.c_void_p, C.POINTER(Stats),
+                                    C.c_int, C.POINTER(C.c_int)]),
     "octmc_status_string": (C.c_char_p, [C.c_int]),
 }
 

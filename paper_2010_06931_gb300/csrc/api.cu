@@ -8,6 +8,9 @@
 // dir, and 4m+5 dot products per iteration).
 #include <algorithm>
 #include <chrono>
+#include <deque>
+#include <map>
+#include <memory>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -162,8 +165,15 @@ struct octmc_lbfgs {
   // One pass over the history: if new_pair, the pair in buffer `spare` is
   // tested (s'y > 1e-12 y'y) and appended (dropping the oldest when full);
   // if g != null, s.g and y.g for every stored pair plus g.g and max|g| are
-  // taken for the next direction.  Returns 1 if a new pair was rejected.
-  int prepare(const double* g, bool new_pair) {
+  // taken for the next direction.  launch_prepare enqueues the dot products
+  // and their copy to pinned host memory; finish_prepare (after the stream
+  // has synchronised) updates the history.  It returns 1 if a new pair was
+  // rejected.
+  bool pend_new = false, pend_g = false;
+  int pend_first_g = 0;
+  std::vector<int> pend_cand;
+
+  void launch_prepare(const double* g, bool new_pair) {
     DotList dl;
     dl.n = 0;
     const int nb = spare;
@@ -180,22 +190,27 @@ struct octmc_lbfgs {
         add(Y[b], Y[nb]);
       }
     }
-    const int first_g = dl.n;
-    std::vector<int> cand = order;
-    if (new_pair) cand.push_back(nb);
+    pend_first_g = dl.n;
+    pend_cand = order;
+    if (new_pair) pend_cand.push_back(nb);
     if (g) {
-      for (int b : cand) {
+      for (int b : pend_cand) {
         add(S[b], g);
         add(Y[b], g);
       }
       add(g, g);
     }
+    pend_new = new_pair;
+    pend_g = (g != nullptr);
     CK(launch_dots(dl, n, g, partials, counter, dots_dev, st));
     CK(cudaMemcpyAsync(dots_host, dots_dev, sizeof(double) * (kMaxDots + 1), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+  }
+
+  int finish_prepare() {
     const double* r = dots_host;
+    const int nb = spare;
     int rejected = 0;
-    if (new_pair) {
+    if (pend_new) {
       const double s_y = r[0], y_y = r[1];
       if (s_y > 1e-12 * y_y && std::isfinite(s_y) && std::isfinite(y_y)) {
         for (size_t t = 0; t < order.size(); t++) {
@@ -213,15 +228,22 @@ struct octmc_lbfgs {
         rejected = 1;
       }
     }
-    if (g) {
-      for (size_t t = 0; t < cand.size(); t++) {
-        sg[cand[t]] = r[first_g + 2 * t];
-        yg[cand[t]] = r[first_g + 2 * t + 1];
+    if (pend_g) {
+      for (size_t t = 0; t < pend_cand.size(); t++) {
+        sg[pend_cand[t]] = r[pend_first_g + 2 * t];
+        yg[pend_cand[t]] = r[pend_first_g + 2 * t + 1];
       }
-      gg = r[first_g + 2 * cand.size()];
+      gg = r[pend_first_g + 2 * pend_cand.size()];
       gmax = r[kMaxDots];
     }
+    pend_new = pend_g = false;
     return rejected;
+  }
+
+  int prepare(const double* g, bool new_pair) {
+    launch_prepare(g, new_pair);
+    CK(cudaStreamSynchronize(st));
+    return finish_prepare();
   }
 
   // dir = -H g (compact form of Byrd, Nocedal & Schnabel with H0 = gamma I),
@@ -494,59 +516,122 @@ void collect_profile(octmc_problem* P) {
   P->prof_pending = false;
 }
 
-// One objective (+ gradient) evaluation.  Enqueues msum -> data -> reg and,
-// if sync, waits and copies the EvalResult to the host.
+// ------------------------------------------------------------ evaluation
+// One objective (+ gradient) evaluation request.
+struct EvalReq {
+  octmc_problem* P;
+  int level;
+  const double* x;
+  double* grad;       // null: objective only
+  const double* dir;  // null: no grad . dir
+  double eta;
+  double delta0;
+};
+
+// Enqueues the evaluations of several problems as one batch: msum, data
+// (one launch per storage dtype) and reg kernels over all of them, then the
+// copy of every EvalResult to its problem's pinned host copy.  A problem
+// may appear once per batch.  Every request gets the same blocks, partition
+// and reduction order as when it is evaluated alone, so its results do not
+// depend on the batch.  The caller synchronises the stream.
+void eval_batch(cudaStream_t st, const std::vector<EvalReq>& reqs) {
+  for (size_t c0 = 0; c0 < reqs.size(); c0 += kMaxSlots) {
+    const int ns = (int)std::min<size_t>(kMaxSlots, reqs.size() - c0);
+    thread_local static MsumMulti MM;
+    thread_local static RegMulti RM;
+    thread_local static DataMulti DM[3];
+    MM.nslots = RM.nslots = ns;
+    MM.b0[0] = RM.b0[0] = 0;
+    int nd[3] = {0, 0, 0};
+    for (int k = 0; k < ns; k++) {
+      const EvalReq& q = reqs[c0 + k];
+      octmc_problem* P = q.P;
+      const Level& Lv = P->lv[q.level];
+      const int64_t n = (int64_t)Lv.dev.w * Lv.dev.h;
+      MsumSlot& ms = MM.sl[k];
+      ms.disp = q.x;
+      ms.plane = n;
+      ms.res = P->res;
+      ms.partials = P->partials;
+      ms.counter = P->counters + 0;
+      MM.b0[k + 1] = MM.b0[k] + msum_grid_blocks();
+      DataArgs A;
+      A.L = Lv.dev;
+      A.disp = q.x;
+      A.str_out = P->str;
+      A.ang_out = P->ang;
+      A.grad = q.grad ? P->gdata : nullptr;
+      A.eta = q.eta;
+      A.delta0 = P->have_ang ? q.delta0 : 0.0;
+      A.eps_h = (float)P->desc.eps_h;
+      A.loss = P->desc.loss;
+      const int dt = Lv.dev.dtype;
+      DM[dt].da[nd[dt]++] = A;
+      RegArgs& R = RM.ra[k];
+      R.L = Lv.dev;
+      R.disp = q.x;
+      R.grad = q.grad;
+      R.gdata = P->gdata;
+      R.dir = q.dir;
+      R.str_in = P->str;
+      R.ang_in = P->ang;
+      R.alpha = P->desc.alpha;
+      R.eps_r = P->desc.eps_r;
+      R.mu = Lv.mu;
+      R.eta = q.eta;
+      R.result = P->res;
+      R.partials = P->partials;
+      R.counter = P->counters + 1;
+      RM.b0[k + 1] = RM.b0[k] + reg_grid_blocks(n);
+    }
+    CK(launch_msum_multi(MM, st));
+    octmc_problem* P0 = reqs[c0].P;
+    const bool prof = (ns == 1 && P0->profile);
+    if (prof) CK(cudaEventRecord(P0->ev0, st));
+    for (int dt = 0; dt < 3; dt++) {
+      if (!nd[dt]) continue;
+      DM[dt].nslots = nd[dt];
+      CK(launch_data_multi(DM[dt], dt, st));
+    }
+    if (prof) {
+      CK(cudaEventRecord(P0->ev1, st));
+      P0->prof_pending = true;
+    }
+    CK(launch_reg_multi(RM, st));
+    for (int k = 0; k < ns; k++) {
+      octmc_problem* P = reqs[c0 + k].P;
+      CK(cudaMemcpyAsync(P->res_host, P->res, sizeof(EvalResult), cudaMemcpyDeviceToHost, st));
+    }
+  }
+}
+
+void collect_profiles(const std::vector<EvalReq>& reqs) {
+  for (const EvalReq& q : reqs)
+    if (q.P->profile) collect_profile(q.P);
+}
+
+// One evaluation of one problem, synchronised (results in P->res_host).
 void eval_impl(octmc_problem* P, int l, const double* disp, double* grad, const double* dir, double eta,
                double delta0, bool sync) {
-  const Level& Lv = P->lv[l];
-  const int64_t n = P->plane(l);
-  CK(launch_msum(disp, n, P->res, P->partials, P->counters + 0, P->st));
-  DataArgs A;
-  A.L = Lv.dev;
-  A.disp = disp;
-  A.str_out = P->str;
-  A.ang_out = P->ang;
-  A.grad = grad ? P->gdata : nullptr;
-  A.eta = eta;
-  A.delta0 = P->have_ang ? delta0 : 0.0;
-  A.eps_h = (float)P->desc.eps_h;
-  A.loss = P->desc.loss;
-  if (P->profile) CK(cudaEventRecord(P->ev0, P->st));
-  CK(launch_data(A, P->st));
-  if (P->profile) {
-    CK(cudaEventRecord(P->ev1, P->st));
-    P->prof_pending = true;
-  }
-  RegArgs R;
-  R.L = Lv.dev;
-  R.disp = disp;
-  R.grad = grad;
-  R.gdata = P->gdata;
-  R.dir = dir;
-  R.str_in = P->str;
-  R.ang_in = P->ang;
-  R.alpha = P->desc.alpha;
-  R.eps_r = P->desc.eps_r;
-  R.mu = Lv.mu;
-  R.eta = eta;
-  R.result = P->res;
-  R.partials = P->partials;
-  R.counter = P->counters + 1;
-  CK(launch_reg(R, P->st));
+  std::vector<EvalReq> r{{P, l, disp, grad, dir, eta, delta0}};
+  eval_batch(P->st, r);
   if (sync) {
-    CK(cudaMemcpyAsync(P->res_host, P->res, sizeof(EvalResult), cudaMemcpyDeviceToHost, P->st));
     CK(cudaStreamSynchronize(P->st));
+    collect_profiles(r);
   }
-  if (P->profile && sync) collect_profile(P);
+}
+
+double eta_from(const EvalResult& r) {
+  const double s = r.terms[0], a = r.terms[1];
+  const double e = std::sqrt(a / s);
+  if (!(s > 0) || !(a > 0) || !std::isfinite(e)) return 1.0;
+  return e;
 }
 
 double eta_impl(octmc_problem* P, int l, const double* disp0) {
   if (!P->have_ang) return 1.0;
   eval_impl(P, l, disp0, nullptr, nullptr, 1.0, 0.5, true);
-  const double s = P->res_host->terms[0], a = P->res_host->terms[1];
-  const double e = std::sqrt(a / s);
-  if (!(s > 0) || !(a > 0) || !std::isfinite(e)) return 1.0;
-  return e;
+  return eta_from(*P->res_host);
 }
 
 void ensure_solver(octmc_problem* P) {
@@ -563,99 +648,222 @@ void ensure_solver(octmc_problem* P) {
   P->opt->init((int64_t)n, P->desc.lbfgs_m, P->st);
 }
 
-// The level solve: same algorithm and constants as the CPU reference solver
-// (weak-Wolfe bisection line search, c1 = 1e-4, c2 = 0.9; a0 = 1/||g|| on an
-// empty history; best Armijo point, else one retry from -g, else stop).
-int solve_impl(octmc_problem* P, int l, double* disp_inout, octmc_stats* st) {
-  const auto t0 = std::chrono::steady_clock::now();
-  ensure_solver(P);
-  const int64_t n = 6 * P->plane(l);
-  octmc_lbfgs* O = P->opt;
-  O->n = n;  // history buffers are level-0 sized; use the first n entries
-  O->reset();
-  const double eta = eta_impl(P, l, disp_inout);
-  P->lv[l].eta = eta;
-  const double delta0 = P->desc.delta0;
-  double *x = P->x, *g = P->g, *xt = P->xt, *gt = P->gt, *xb = P->xb, *gb = P->gb, *dir = P->dir;
-  CK(cudaMemcpyAsync(x, disp_inout, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->st));
-  eval_impl(P, l, x, g, nullptr, eta, delta0, true);
-  double f = P->res_host->terms[4];
-  int evals = 1, iters = 0, status = 1, small = 0, retried = 0;
-  O->prepare(g, false);
-  while (iters < P->desc.max_iter) {
-    if (O->gmax <= P->desc.gtol) {
-      status = 0;
-      break;
+}  // namespace
+
+// ------------------------------------------------------------ solve machine
+// The L-BFGS solve of one problem as a state machine that needs exactly one
+// objective evaluation per step, so that one problem can be solved alone
+// (octmc_solve_level / octmc_solve_full) or many together in batched steps
+// (octmc_server_*) with the same algorithm and the same results.
+//
+// Algorithm and constants are those of the CPU reference solver: eta at the
+// start of each level (Eq. 10), weak-Wolfe bisection line search (c1 = 1e-4,
+// c2 = 0.9), a0 = 1/||g|| on an empty history, else 1; after max_ls trials
+// the best Armijo point, else one retry from -g, else stop; stop on
+// max|g| <= gtol, 3 iterations of relative decrease < ftol, or max_iter.
+struct SolveMachine {
+  enum Phase { ETA, INIT, TRIAL, DONE };
+  octmc_problem* P = nullptr;
+  int level = 0, last_level = 0;
+  double* out = nullptr;  // result (device), level `last_level` layout
+  Phase ph = DONE;
+  int rc = OCTMC_OK;
+  bool dots_pending = false;
+  int dots_kind = 0;  // 1: direction after reset/start, 2: after an accepted step
+  double *x, *g, *xt, *gt, *xb, *gb, *dir;
+  double f = 0, dg0 = 0, a = 0, lo = 0, hi = 0, fb = 0, ft = 0, eta = 1.0;
+  bool have_lo = false;
+  int ls = 0, iters = 0, evals = 0, small = 0, retried = 0, status = 1;
+  std::chrono::steady_clock::time_point t_level;
+  std::vector<octmc_stats> stats;
+
+  int64_t n() const { return 6 * P->plane(level); }
+
+  // Starts at `level` from the device field `init` (level layout), or from
+  // zero when init is null, and runs down to `last` (inclusive); the result
+  // goes to `result` (device, level `last` layout).
+  void start(octmc_problem* p, int first, int last, const double* init, double* result) {
+    P = p;
+    ensure_solver(P);
+    x = P->x; g = P->g; xt = P->xt; gt = P->gt; xb = P->xb; gb = P->gb; dir = P->dir;
+    level = first;
+    last_level = last;
+    out = result;
+    stats.clear();
+    rc = OCTMC_OK;
+    if (init) CK(cudaMemcpyAsync(x, init, sizeof(double) * n(), cudaMemcpyDeviceToDevice, P->st));
+    else CK(cudaMemsetAsync(x, 0, sizeof(double) * n(), P->st));
+    begin_level();
+  }
+
+  void begin_level() {
+    t_level = std::chrono::steady_clock::now();
+    P->opt->n = n();  // history buffers are level-0 sized; use the first n entries
+    P->opt->reset();
+    iters = evals = small = retried = 0;
+    status = 1;
+    dots_pending = false;
+    eta = 1.0;
+    ph = P->have_ang ? ETA : INIT;
+  }
+
+  EvalReq request() const {
+    if (ph == ETA) return {P, level, x, nullptr, nullptr, 1.0, 0.5};
+    if (ph == INIT) return {P, level, x, g, nullptr, eta, P->desc.delta0};
+    return {P, level, xt, gt, dir, eta, P->desc.delta0};
+  }
+
+  void want_dots(const double* gv, bool new_pair, int kind) {
+    P->opt->launch_prepare(gv, new_pair);
+    dots_pending = true;
+    dots_kind = kind;
+  }
+
+  void on_eval() {
+    const EvalResult& r = *P->res_host;
+    if (ph == ETA) {
+      eta = eta_from(r);
+      P->lv[level].eta = eta;
+      ph = INIT;
+      return;
     }
-    const int k = O->k();
-    const double dg0 = O->direction(g, dir);
-    double a = (O->k() == 0) ? 1.0 / std::sqrt(O->gg) : 1.0;
-    (void)k;
-    double lo = 0.0, hi = std::numeric_limits<double>::infinity(), ft = 0.0, fb = 0.0;
-    bool accepted = false, have_lo = false;
-    for (int ls = 0; ls < P->desc.max_ls; ls++) {
-      CK(launch_axpy(x, a, dir, xt, n, P->st));
-      eval_impl(P, l, xt, gt, dir, eta, delta0, true);
-      evals++;
-      ft = P->res_host->terms[4];
-      const double dgt = P->res_host->gdir;
-      if (!(ft <= f + 1e-4 * a * dg0)) {
-        hi = a;
-        a = 0.5 * (lo + hi);
-      } else if (dgt < 0.9 * dg0) {
-        lo = a;
-        have_lo = true;
-        fb = ft;
-        std::swap(xb, xt);
-        std::swap(gb, gt);
-        a = std::isinf(hi) ? 2.0 * a : 0.5 * (lo + hi);
-      } else {
-        accepted = true;
-        break;
-      }
+    evals++;
+    if (ph == INIT) {
+      f = r.terms[4];
+      want_dots(g, false, 1);
+      return;
+    }
+    // TRIAL
+    ft = r.terms[4];
+    const double dgt = r.gdir;
+    ls++;
+    bool accepted = false;
+    if (!(ft <= f + 1e-4 * a * dg0)) {
+      hi = a;
+      a = 0.5 * (lo + hi);
+    } else if (dgt < 0.9 * dg0) {
+      lo = a;
+      have_lo = true;
+      fb = ft;
+      std::swap(xb, xt);
+      std::swap(gb, gt);
+      a = std::isinf(hi) ? 2.0 * a : 0.5 * (lo + hi);
+    } else {
+      accepted = true;
+    }
+    if (!accepted && ls < P->desc.max_ls) {
+      CK(launch_axpy(x, a, dir, xt, n(), P->st));
+      return;
     }
     if (!accepted) {
       if (have_lo) {
         std::swap(xt, xb);
         std::swap(gt, gb);
         ft = fb;
-      } else if (O->k() > 0 && !retried) {
-        O->reset();
+      } else if (P->opt->k() > 0 && !retried) {
+        P->opt->reset();
         retried = 1;
-        O->prepare(g, false);
-        continue;
+        want_dots(g, false, 1);
+        return;
       } else {
         status = 2;
-        break;
+        end_level();
+        return;
       }
     }
     retried = 0;
-    CK(launch_sub2(xt, x, gt, g, O->S[O->spare], O->Y[O->spare], n, P->st));
+    octmc_lbfgs* O = P->opt;
+    CK(launch_sub2(xt, x, gt, g, O->S[O->spare], O->Y[O->spare], n(), P->st));
     const double rel = (f - ft) / std::max(std::max(std::fabs(f), std::fabs(ft)), 1.0);
     std::swap(x, xt);
     std::swap(g, gt);
     f = ft;
     iters++;
-    O->prepare(g, true);
     small = (rel < P->desc.ftol) ? small + 1 : 0;
-    if (small >= 3) {
+    want_dots(g, true, 2);
+  }
+
+  void on_dots() {
+    dots_pending = false;
+    P->opt->finish_prepare();
+    if (dots_kind == 2 && small >= 3) {
       status = 0;
-      break;
+      end_level();
+      return;
+    }
+    // top of an iteration
+    if (iters >= P->desc.max_iter) {
+      status = 1;
+      end_level();
+      return;
+    }
+    if (P->opt->gmax <= P->desc.gtol) {
+      status = 0;
+      end_level();
+      return;
+    }
+    dg0 = P->opt->direction(g, dir);
+    a = (P->opt->k() == 0) ? 1.0 / std::sqrt(P->opt->gg) : 1.0;
+    lo = 0.0;
+    hi = std::numeric_limits<double>::infinity();
+    have_lo = false;
+    ls = 0;
+    CK(launch_axpy(x, a, dir, xt, n(), P->st));
+    ph = TRIAL;
+  }
+
+  void end_level() {
+    octmc_stats s{};
+    s.level = level;
+    s.iters = iters;
+    s.evals = evals;
+    s.status = status;
+    s.f = f;
+    s.eta = eta;
+    s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_level).count();
+    stats.push_back(s);
+    if (!std::isfinite(f)) rc = OCTMC_ERR_NONFINITE;
+    else if (status == 1 && rc == OCTMC_OK) rc = OCTMC_NOT_CONVERGED;
+    if (level == last_level || rc < 0) {
+      CK(cudaMemcpyAsync(out, x, sizeof(double) * n(), cudaMemcpyDeviceToDevice, P->st));
+      ph = DONE;
+      return;
+    }
+    // prolong to the next finer level (xt is free here)
+    const LevelDev& C = P->lv[level].dev;
+    const LevelDev& F = P->lv[level - 1].dev;
+    CK(launch_prolong(x, C.w, C.h, xt, F.w, F.h, P->st));
+    std::swap(x, xt);
+    level--;
+    begin_level();
+  }
+};
+
+namespace {
+
+// Drives one machine to completion.
+int run_machine(SolveMachine& M) {
+  while (M.ph != SolveMachine::DONE) {
+    std::vector<EvalReq> r{M.request()};
+    eval_batch(M.P->st, r);
+    CK(cudaStreamSynchronize(M.P->st));
+    collect_profiles(r);
+    M.on_eval();
+    while (M.dots_pending) {
+      CK(cudaStreamSynchronize(M.P->st));
+      M.on_dots();
     }
   }
-  CK(cudaMemcpyAsync(disp_inout, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->st));
-  CK(cudaStreamSynchronize(P->st));
-  if (st) {
-    st->level = l;
-    st->iters = iters;
-    st->evals = evals;
-    st->status = status;
-    st->f = f;
-    st->eta = eta;
-    st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  }
-  if (!std::isfinite(f)) return OCTMC_ERR_NONFINITE;
-  return status == 1 ? OCTMC_NOT_CONVERGED : OCTMC_OK;
+  CK(cudaStreamSynchronize(M.P->st));
+  return M.rc;
+}
+
+int solve_impl(octmc_problem* P, int l, double* disp_inout, octmc_stats* st) {
+  SolveMachine M;
+  M.start(P, l, l, disp_inout, disp_inout);
+  const int rc = run_machine(M);
+  if (st && !M.stats.empty()) *st = M.stats.back();
+  return rc;
 }
 
 template <typename F>
@@ -675,6 +883,132 @@ int guarded(F&& f) {
 bool valid_level(const octmc_problem* p, int level) { return p && level >= 0 && level < (int)p->lv.size(); }
 
 }  // namespace
+
+// ====================================================================== server
+// Continuous batching of independent solves: requests wait in a FIFO queue
+// and are admitted (their problem created on the device) while a slot is
+// free and their estimated device memory fits the budget; every step runs
+// one batched objective evaluation for all admitted requests -- each at its
+// own level, iteration and line-search trial -- followed by each request's
+// L-BFGS bookkeeping.  Finished results stay on the device until polled.
+namespace {
+
+int64_t estimate_bytes_impl(const octmc_desc& D) {
+  int64_t w = D.w, h = D.h, d = D.d, total = 0, peak_tmp = 0;
+  const int64_t sbytes = D.storage == OCTMC_F32 ? 4 : 2;
+  const int64_t n0 = w * h;
+  for (int l = 0; l < std::max(D.levels, 1); l++) {
+    const int64_t cols = w * h, dp = (d + 3) & ~int64_t(3);
+    total += 2 * cols * dp * sbytes + cols * (2 * 4 + 2 * (4 + 4 + 4 + 4)) + (w + h) * 4;
+    if (D.storage != OCTMC_F32) peak_tmp += 2 * cols * dp * 4;
+    w = (w + 1) / 2;
+    h = (h + 1) / 2;
+    d = (d + 1) / 2;
+  }
+  const int64_t m = std::max(D.lbfgs_m, 1);
+  total += n0 * (4 + 4 + 24);                       // per-A-scan partials, float gradient
+  total += (7 + 2 * (m + 1) + 1) * 6 * n0 * 8;      // solver vectors, history, result
+  total += 64 << 10;                                // small buffers
+  return total + peak_tmp;
+}
+
+}  // namespace
+
+struct octmc_server {
+  struct Req {
+    int64_t ticket;
+    octmc_desc desc;
+    int64_t bytes;
+    octmc_problem* P = nullptr;
+    double* result = nullptr;
+    std::unique_ptr<SolveMachine> M;
+    int state = OCTMC_REQ_QUEUED;
+    int rc = OCTMC_OK;
+  };
+  cudaStream_t st = nullptr;
+  int64_t budget = 0, in_use = 0;
+  int max_slots = 1;
+  int64_t next_ticket = 1;
+  std::deque<std::shared_ptr<Req>> queue;
+  std::vector<std::shared_ptr<Req>> active;
+  std::map<int64_t, std::shared_ptr<Req>> all;
+
+  void release(Req& r) {
+    if (r.P) {
+      cudaStreamSynchronize(st);
+      delete r.P;
+      r.P = nullptr;
+    }
+    dfree(r.result);
+    r.result = nullptr;
+    in_use -= r.bytes;
+    r.bytes = 0;
+  }
+
+  ~octmc_server() {
+    if (st) cudaStreamSynchronize(st);
+    else cudaDeviceSynchronize();
+    for (auto& kv : all) release(*kv.second);
+  }
+
+  void admit() {
+    while (!queue.empty() && (int)active.size() < max_slots) {
+      auto r = queue.front();
+      if (in_use + r->bytes > budget) break;  // wait for memory (finished results count until polled)
+      queue.pop_front();
+      in_use += r->bytes;
+      octmc_desc D = r->desc;
+      D.stream = st;
+      r->P = new octmc_problem();
+      r->P->desc = D;
+      r->P->st = st;
+      r->P->have_ang = (D.ax != nullptr);
+      try {
+        create_impl(r->P);
+        r->result = dalloc<double>((size_t)6 * D.w * D.h);
+        r->M.reset(new SolveMachine());
+        r->M->start(r->P, D.levels - 1, 0, nullptr, r->result);
+        r->state = OCTMC_REQ_RUNNING;
+        active.push_back(r);
+      } catch (const CudaFail& e) {
+        cudaGetLastError();
+        r->rc = e.code;
+        r->state = OCTMC_REQ_DONE;
+        release(*r);
+      }
+    }
+  }
+
+  void step() {
+    admit();
+    if (active.empty()) return;
+    std::vector<EvalReq> reqs;
+    reqs.reserve(active.size());
+    for (auto& r : active) reqs.push_back(r->M->request());
+    eval_batch(st, reqs);
+    CK(cudaStreamSynchronize(st));
+    bool dots = false;
+    for (auto& r : active) {
+      r->M->on_eval();
+      dots |= r->M->dots_pending;
+    }
+    if (dots) {
+      CK(cudaStreamSynchronize(st));
+      for (auto& r : active)
+        if (r->M->dots_pending) r->M->on_dots();
+    }
+    std::vector<std::shared_ptr<Req>> still;
+    for (auto& r : active) {
+      if (r->M->ph == SolveMachine::DONE) {
+        r->rc = r->M->rc;
+        r->state = OCTMC_REQ_DONE;
+      } else {
+        still.push_back(r);
+      }
+    }
+    active.swap(still);
+  }
+};
 
 // ====================================================================== C ABI
 extern "C" {
@@ -794,25 +1128,12 @@ int octmc_solve_full(octmc_problem* p, double* disp_out, octmc_stats* st) {
   if (!p || !disp_out) return OCTMC_ERR_INVALID_ARG;
   return guarded([&] {
     const int L = (int)p->lv.size();
-    ensure_solver(p);
-    // coarse-to-fine: the level field lives in p->xb's twin buffers; use dir
-    // as the coarse copy while prolonging
-    double* cur = disp_out;  // level-0 sized by contract
-    CK(cudaMemsetAsync(cur, 0, sizeof(double) * 6 * p->plane(L - 1), p->st));
-    int worst = OCTMC_OK;
-    for (int l = L - 1; l >= 0; l--) {
-      if (l != L - 1) {
-        CK(cudaMemcpyAsync(p->dir, cur, sizeof(double) * 6 * p->plane(l + 1), cudaMemcpyDeviceToDevice, p->st));
-        CK(launch_prolong(p->dir, p->lv[l + 1].dev.w, p->lv[l + 1].dev.h, cur, p->lv[l].dev.w,
-                          p->lv[l].dev.h, p->st));
-      }
-      octmc_stats s{};
-      const int rc = solve_impl(p, l, cur, &s);
-      if (st) st[L - 1 - l] = s;
-      if (rc < 0) return rc;
-      if (rc == OCTMC_NOT_CONVERGED) worst = rc;
-    }
-    return worst;
+    SolveMachine M;
+    M.start(p, L - 1, 0, nullptr, disp_out);
+    const int rc = run_machine(M);
+    if (st)
+      for (size_t k = 0; k < M.stats.size(); k++) st[k] = M.stats[k];
+    return rc;
   });
 }
 
@@ -904,6 +1225,97 @@ int octmc_profile_read(octmc_problem* p, double* total_ms, long long* launches) 
   if (total_ms) *total_ms = p->prof_ms;
   if (launches) *launches = p->prof_count;
   return OCTMC_OK;
+}
+
+int64_t octmc_estimate_bytes(const octmc_desc* desc) {
+  if (!desc || desc->w < 1 || desc->h < 1 || desc->d < 1) return -1;
+  return estimate_bytes_impl(*desc);
+}
+
+int octmc_server_create(int64_t budget_bytes, int max_slots, void* stream, octmc_server** out) {
+  if (!out || budget_bytes <= 0 || max_slots < 1) return OCTMC_ERR_INVALID_ARG;
+  *out = nullptr;
+  octmc_server* s = new (std::nothrow) octmc_server();
+  if (!s) return OCTMC_ERR_OOM;
+  s->st = (cudaStream_t)stream;
+  s->budget = budget_bytes;
+  s->max_slots = std::min(max_slots, 1 << 16);
+  const int rc = guarded([&] {
+    check_device();
+    return OCTMC_OK;
+  });
+  if (rc != OCTMC_OK) {
+    delete s;
+    return rc;
+  }
+  *out = s;
+  return OCTMC_OK;
+}
+
+void octmc_server_destroy(octmc_server* s) { delete s; }
+
+int octmc_server_submit(octmc_server* s, const octmc_desc* desc, int64_t* ticket) {
+  if (!s || !desc || !ticket) return OCTMC_ERR_INVALID_ARG;
+  const octmc_desc& D = *desc;
+  if (D.w < 1 || D.h < 1 || D.d < 1 || !D.sx || !D.sy || !D.tx || !D.ty || (D.ax == nullptr) != (D.ay == nullptr) ||
+      D.levels < 1 || D.levels > 16 || D.lbfgs_m < 1 || D.lbfgs_m > 32 || D.max_ls < 1 || D.max_iter < 0 ||
+      (D.loss != OCTMC_LOSS_PSEUDO_HUBER && D.loss != OCTMC_LOSS_SSD) ||
+      (D.storage != OCTMC_F32 && D.storage != OCTMC_BF16 && D.storage != OCTMC_F16) || !(D.eps_h > 0) ||
+      !(D.eps_r > 0) || !(D.alpha >= 0) || !(D.delta0 >= 0))
+    return OCTMC_ERR_INVALID_ARG;
+  auto r = std::make_shared<octmc_server::Req>();
+  r->ticket = s->next_ticket++;
+  r->desc = D;
+  r->bytes = estimate_bytes_impl(D);
+  if (r->bytes > s->budget) return OCTMC_ERR_OOM;  // could never be admitted
+  s->queue.push_back(r);
+  s->all[r->ticket] = r;
+  *ticket = r->ticket;
+  return OCTMC_OK;
+}
+
+int octmc_server_step(octmc_server* s, int* active, int* queued) {
+  if (!s) return OCTMC_ERR_INVALID_ARG;
+  const int rc = guarded([&] {
+    s->step();
+    return OCTMC_OK;
+  });
+  if (active) *active = (int)s->active.size();
+  if (queued) *queued = (int)s->queue.size();
+  return rc;
+}
+
+int octmc_server_state(const octmc_server* s, int64_t ticket, int* state) {
+  if (!s || !state) return OCTMC_ERR_INVALID_ARG;
+  auto it = s->all.find(ticket);
+  *state = (it == s->all.end()) ? OCTMC_REQ_UNKNOWN : it->second->state;
+  return OCTMC_OK;
+}
+
+int octmc_server_poll(octmc_server* s, int64_t ticket, int* state, double* disp_out, octmc_stats* stats, int max_stats,
+                      int* req_rc) {
+  if (!s || !state) return OCTMC_ERR_INVALID_ARG;
+  auto it = s->all.find(ticket);
+  if (it == s->all.end()) {
+    *state = OCTMC_REQ_UNKNOWN;
+    return OCTMC_OK;
+  }
+  octmc_server::Req& r = *it->second;
+  *state = r.state;
+  if (r.state != OCTMC_REQ_DONE) return OCTMC_OK;
+  const int rc = guarded([&] {
+    if (disp_out && r.result)
+      CK(cudaMemcpyAsync(disp_out, r.result, sizeof(double) * 6 * r.desc.w * r.desc.h, cudaMemcpyDeviceToDevice,
+                         s->st));
+    CK(cudaStreamSynchronize(s->st));
+    if (stats && r.M)
+      for (int k = 0; k < max_stats && k < (int)r.M->stats.size(); k++) stats[k] = r.M->stats[k];
+    return OCTMC_OK;
+  });
+  if (req_rc) *req_rc = r.rc;
+  s->release(r);
+  s->all.erase(it);
+  return rc;
 }
 
 const char* octmc_status_string(int code) {

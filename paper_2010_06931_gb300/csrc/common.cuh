@@ -202,7 +202,42 @@ struct RegArgs {
   unsigned* counter;      // zero-initialised, reset by the last block
 };
 
+// Batched evaluation of several problems ("slots") in one launch per
+// kernel.  Data kernel: slot s owns the A-scans [begin[s], begin[s+1]) of
+// the launch.  Reduction kernels: slot s owns the blocks [b0[s], b0[s+1]) --
+// the same number and partition of blocks as a launch for that slot alone,
+// so its sums do not depend on the other slots.  The arguments travel in the
+// kernel parameter block (at most 32 KB).
+constexpr int kMaxSlots = 48;
+struct DataMulti {
+  int nslots;
+  int64_t total;
+  int64_t begin[kMaxSlots + 1];
+  DataArgs da[kMaxSlots];
+};
+struct MsumSlot {
+  const double* disp;
+  int64_t plane;
+  EvalResult* res;
+  double* partials;
+  unsigned* counter;
+};
+struct MsumMulti {
+  int nslots;
+  int b0[kMaxSlots + 1];
+  MsumSlot sl[kMaxSlots];
+};
+struct RegMulti {
+  int nslots;
+  int b0[kMaxSlots + 1];
+  RegArgs ra[kMaxSlots];
+};
+
 // ---------------------------------------------------------------- launchers
+// all slots of one data launch share the storage dtype
+cudaError_t launch_data_multi(const DataMulti& M, int dtype, cudaStream_t s);
+cudaError_t launch_msum_multi(const MsumMulti& M, cudaStream_t s);
+cudaError_t launch_reg_multi(const RegMulti& M, cudaStream_t s);
 cudaError_t launch_data(const DataArgs& a, cudaStream_t s);
 cudaError_t launch_msum(const double* disp, int64_t plane, EvalResult* res, double* partials,
                         unsigned* counter, cudaStream_t s);

@@ -206,14 +206,11 @@ __device__ __forceinline__ void sample_block(const Vol& V, int kb, int lane, int
 #ifndef OCTMC_DATA_MINB
 #define OCTMC_DATA_MINB 3
 #endif
+// The whole data-term computation of output A-scan p by one warp.
 template <typename T>
-__global__ void __launch_bounds__(kWarpsPerBlock * kWarp, OCTMC_DATA_MINB)
-data_kernel(const DataArgs A) {
+__device__ __forceinline__ void data_ascan(const DataArgs& A, int64_t p, int lane) {
   const LevelDev& L = A.L;
-  const int lane = threadIdx.x & 31;
   const int64_t nasc = (int64_t)L.w * L.h;
-  const int64_t p = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-  if (p >= nasc) return;  // warp-uniform
   const int i = (int)(p % L.w), j = (int)(p / L.w);
 
   int base[6];
@@ -351,7 +348,45 @@ data_kernel(const DataArgs A) {
   else if (lane < 8 && A.grad) A.grad[(int64_t)(lane - 2) * nasc + p] = out;
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kWarpsPerBlock * kWarp, OCTMC_DATA_MINB)
+data_kernel(const DataArgs A) {
+  const int64_t p = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (p >= (int64_t)A.L.w * A.L.h) return;  // warp-uniform
+  data_ascan<T>(A, p, threadIdx.x & 31);
+}
+
+// Several problems ("slots") in one launch: grid (x, slots), block
+// (x, s) takes A-scans x*8 .. x*8+7 of slot s (blocks past a slot's end exit
+// at once).  The slots' arguments travel in the kernel's parameter block and
+// the slot index is uniform per block.  Each A-scan's result does not depend
+// on which other slots are in the launch.
+template <typename T>
+__global__ void __launch_bounds__(kWarpsPerBlock * kWarp, OCTMC_DATA_MINB)
+data_multi_kernel(const __grid_constant__ DataMulti M) {
+  const DataArgs& A = M.da[blockIdx.y];
+  const int64_t p = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (p >= (int64_t)A.L.w * A.L.h) return;  // warp-uniform
+  data_ascan<T>(A, p, threadIdx.x & 31);
+}
+
 }  // namespace
+
+cudaError_t launch_data_multi(const DataMulti& M, int dtype, cudaStream_t s) {
+  if (M.nslots <= 0) return cudaSuccess;
+  int64_t most = 0;
+  for (int k = 0; k < M.nslots; k++) most = max(most, (int64_t)M.da[k].L.w * M.da[k].L.h);
+  const int64_t bx = (most + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  if (bx <= 0) return cudaSuccess;
+  const dim3 g((unsigned)bx, (unsigned)M.nslots);
+  if (dtype == OCTMC_BF16)
+    data_multi_kernel<__nv_bfloat16><<<g, kWarpsPerBlock * kWarp, 0, s>>>(M);
+  else if (dtype == OCTMC_F16)
+    data_multi_kernel<__half><<<g, kWarpsPerBlock * kWarp, 0, s>>>(M);
+  else
+    data_multi_kernel<float><<<g, kWarpsPerBlock * kWarp, 0, s>>>(M);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_data(const DataArgs& a, cudaStream_t s) {
   const int64_t nasc = (int64_t)a.L.w * a.L.h;

@@ -51,12 +51,12 @@ __device__ void block_sum(double (&v)[N]) {
   __syncthreads();
 }
 
-// True in every thread of the last block to finish (partials visible).
-__device__ bool last_block(unsigned* counter) {
+// True in every thread of the last of nblk blocks to finish (partials visible).
+__device__ bool last_block(unsigned* counter, int nblk) {
   __shared__ bool is_last;
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) is_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  if (threadIdx.x == 0) is_last = (atomicAdd(counter, 1u) == (unsigned)nblk - 1u);
   __syncthreads();
   if (is_last) __threadfence();
   return is_last;
@@ -74,26 +74,48 @@ __device__ void sum_partials(const double* partials, int nblocks, double (&v)[N]
   block_sum<N>(v);
 }
 
-__global__ void __launch_bounds__(kThreads) msum_kernel(const double* __restrict__ disp, int64_t plane,
-                                                        EvalResult* res, double* partials,
-                                                        unsigned* counter) {
+// Block blk of nblk blocks working on one problem's mean-term sums.
+__device__ void msum_body(const double* __restrict__ disp, int64_t plane, EvalResult* res, double* partials,
+                          unsigned* counter, int blk, int nblk) {
   float f[3] = {0.f, 0.f, 0.f};
-  for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < plane;
-       e += (int64_t)gridDim.x * kThreads) {
+  for (int64_t e = (int64_t)blk * kThreads + threadIdx.x; e < plane; e += (int64_t)nblk * kThreads) {
 #pragma unroll
     for (int c = 0; c < 3; c++) f[c] += narrow_trunc(disp[c * plane + e]) + narrow_trunc(disp[(3 + c) * plane + e]);
   }
   double v[3] = {widen_exact(f[0]), widen_exact(f[1]), widen_exact(f[2])};
   block_sum<3>(v);
   if (threadIdx.x == 0)
-    for (int c = 0; c < 3; c++) partials[blockIdx.x * 3 + c] = v[c];
-  if (last_block(counter)) {
-    sum_partials<3>(partials, gridDim.x, v);
+    for (int c = 0; c < 3; c++) partials[blk * 3 + c] = v[c];
+  if (last_block(counter, nblk)) {
+    sum_partials<3>(partials, nblk, v);
     if (threadIdx.x == 0) {
       for (int c = 0; c < 3; c++) res->msum[c] = v[c];
       *counter = 0u;
     }
   }
+}
+
+__global__ void __launch_bounds__(kThreads) msum_kernel(const double* __restrict__ disp, int64_t plane,
+                                                        EvalResult* res, double* partials,
+                                                        unsigned* counter) {
+  msum_body(disp, plane, res, partials, counter, blockIdx.x, gridDim.x);
+}
+
+// Slot of block b: the last s with b0[s] <= b (block-uniform).
+__device__ __forceinline__ int slot_of(const int* b0, int nslots, int b) {
+  int lo = 0, hi = nslots - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (b0[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kThreads) msum_multi_kernel(const __grid_constant__ MsumMulti M) {
+  const int s = slot_of(M.b0, M.nslots, blockIdx.x);
+  const MsumSlot& S = M.sl[s];
+  msum_body(S.disp, S.plane, S.res, S.partials, S.counter, blockIdx.x - M.b0[s], M.b0[s + 1] - M.b0[s]);
 }
 
 // Pseudo-Huber loss (and derivative) of a displacement difference.
@@ -105,7 +127,7 @@ __device__ __forceinline__ float huber(float x, float inv_eps, float* dl) {
   return __fdividef(x * r, fmaf(q, is, 1.0f));
 }
 
-__global__ void __launch_bounds__(kThreads) reg_kernel(const RegArgs A) {
+__device__ void reg_body(const RegArgs& A, int blk, int nblk) {
   const LevelDev& L = A.L;
   const int64_t n = (int64_t)L.w * L.h;
   const float inv_eps = (float)(1.0 / A.eps_r);
@@ -114,8 +136,7 @@ __global__ void __launch_bounds__(kThreads) reg_kernel(const RegArgs A) {
 #pragma unroll
   for (int c = 0; c < 3; c++) two_mu_s[c] = (float)(2.0 * A.mu * A.result->msum[c]);
   double v[4] = {0.0, 0.0, 0.0, 0.0};  // S^str, S^ang, R, grad . dir
-  for (int64_t p = (int64_t)blockIdx.x * kThreads + threadIdx.x; p < n;
-       p += (int64_t)gridDim.x * kThreads) {
+  for (int64_t p = (int64_t)blk * kThreads + threadIdx.x; p < n; p += (int64_t)nblk * kThreads) {
     float r = 0.f, gd = 0.f;
 #pragma unroll
     for (int V = 0; V < 2; V++) {
@@ -152,9 +173,9 @@ __global__ void __launch_bounds__(kThreads) reg_kernel(const RegArgs A) {
   }
   block_sum<4>(v);
   if (threadIdx.x == 0)
-    for (int c = 0; c < 4; c++) A.partials[blockIdx.x * 4 + c] = v[c];
-  if (last_block(A.counter)) {
-    sum_partials<4>(A.partials, gridDim.x, v);
+    for (int c = 0; c < 4; c++) A.partials[blk * 4 + c] = v[c];
+  if (last_block(A.counter, nblk)) {
+    sum_partials<4>(A.partials, nblk, v);
     if (threadIdx.x == 0) {
       const double* ms = A.result->msum;
       const double M = A.mu * (ms[0] * ms[0] + ms[1] * ms[1] + ms[2] * ms[2]);
@@ -171,9 +192,28 @@ __global__ void __launch_bounds__(kThreads) reg_kernel(const RegArgs A) {
   }
 }
 
+__global__ void __launch_bounds__(kThreads) reg_kernel(const RegArgs A) { reg_body(A, blockIdx.x, gridDim.x); }
+
+__global__ void __launch_bounds__(kThreads) reg_multi_kernel(const __grid_constant__ RegMulti M) {
+  const int s = slot_of(M.b0, M.nslots, blockIdx.x);
+  reg_body(M.ra[s], blockIdx.x - M.b0[s], M.b0[s + 1] - M.b0[s]);
+}
+
 }  // namespace
 
 int msum_grid_blocks() { return kMsumBlocks; }
+
+cudaError_t launch_msum_multi(const MsumMulti& M, cudaStream_t s) {
+  if (M.nslots <= 0 || M.b0[M.nslots] <= 0) return cudaSuccess;
+  msum_multi_kernel<<<M.b0[M.nslots], kThreads, 0, s>>>(M);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reg_multi(const RegMulti& M, cudaStream_t s) {
+  if (M.nslots <= 0 || M.b0[M.nslots] <= 0) return cudaSuccess;
+  reg_multi_kernel<<<M.b0[M.nslots], kThreads, 0, s>>>(M);
+  return cudaGetLastError();
+}
 
 int reg_grid_blocks(int64_t n) {
   int64_t b = (n + kThreads - 1) / kThreads;

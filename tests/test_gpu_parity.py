@@ -206,3 +206,20 @@ def test_solve_level_parity_c1(c1, loss):
     assert rms <= 0.05, (rms, st, stc)
     # secondary sanity check: both stop at the iteration cap, trajectories differ by rounding
     assert st["f"] == pytest.approx(stc["f"], rel=5e-3)
+
+
+def test_solve_full_parity_clinical_size():
+    # the bench workload (300 x 300 x 512, 3 levels) through the whole
+    # coarse-to-fine path on both sides: same start, same algorithm, 30
+    # iterations per level
+    p, cfg = make_config("c2")
+    kw = dict(alpha=0.1, loss=0)
+    G = gpu_problem(p, levels=3, max_iter=30, **kw)
+    C = cpu_problem(p, **kw)
+    Dg, st = G.solve_full()
+    Dc, stc = C.solve_full(3, max_iter=30)
+    rms = float(np.sqrt(((Dg.cpu().numpy() - Dc) ** 2).mean()))
+    print("c2 solve_full: GPU vs oracle RMS %.4f px; GPU %s; oracle %s" % (rms, st, stc))
+    for a, b in zip(st, stc):
+        assert a["eta"] == pytest.approx(b["eta"], rel=F_TOL)
+    assert rms <= 0.05
