@@ -167,13 +167,32 @@ def _interp_motion(m, s):
     return (1 - f) * m[s0] + f * m[np.minimum(s0 + 1, n - 1)]
 
 
+def _render_torch(retina, x, y, z0, d, speckle, gen, device):
+    """The retina intensity (and speckle) of A-scans at (x, y) on a torch device."""
+    import torch
+    surf = torch.from_numpy(retina.surfaces(x, y).astype(np.float32)).to(device)
+    z = torch.arange(d, dtype=torch.float32, device=device) + torch.from_numpy(
+        np.asarray(z0, dtype=np.float32)).to(device)[..., None]
+    out = torch.full(z.shape, float(retina.levels[0]), dtype=torch.float32, device=device)
+    steps = np.diff(retina.levels)
+    for l in range(retina.n + 1):
+        out += float(steps[l]) * torch.special.ndtr((z - surf[..., l:l + 1]) / retina.sigma)
+    if speckle:
+        u = torch.rand(out.shape, generator=gen, device=device, dtype=torch.float32).clamp_min_(1e-12)
+        out *= math.sqrt(2.0 / math.pi) * torch.sqrt(-2.0 * torch.log(u))  # unit-mean Rayleigh
+    return out
+
+
 def make_pair(w, h, d, n_layers=8, n_slabs=2, n_saccades=2, max_saccade=5.0, drift_sigma=0.02,
-              seed=0, speckle=True, row_chunk=16, **_unused):
+              seed=0, speckle=True, row_chunk=16, device=None, **_unused):
     """Render one orthogonal scan pair.
 
     Returns a dict with float32 ``sx, sy [h][w][d]``, ``ax, ay [h][w]``,
     ``vx [h]``, ``vy [w]``, float64 ``tx, ty [h][w]`` and the motion
-    (``mx, my`` per slot, [n][3]) with the saccade slots.
+    (``mx, my`` per slot, [n][3]) with the saccade slots.  With ``device``
+    (a torch device) the volumes are rendered there and returned as torch
+    tensors (same structure and parameters; speckle from torch's generator),
+    which is much faster for large pairs.
     """
     rng = np.random.default_rng(seed)
     retina = _Retina(rng, w, h, d, n_layers)
@@ -195,9 +214,18 @@ def make_pair(w, h, d, n_layers=8, n_slabs=2, n_saccades=2, max_saccade=5.0, dri
 
     out = {}
     for name, m, tmap, sac, slow_len in (("x", mx, tx, sacx, h), ("y", my, ty, sacy, w)):
-        vol = np.empty((h, w, d), dtype=np.float32)
-        srng = np.random.default_rng(seed * 7919 + (1 if name == "x" else 2))
-        for j0 in range(0, h, row_chunk):
+        if device is not None:
+            import torch
+            gen = torch.Generator(device=device)
+            gen.manual_seed(seed * 7919 + (1 if name == "x" else 2))
+            s = tmap.astype(np.int64)
+            mv = m[s]
+            jj, ii = np.meshgrid(np.arange(h), np.arange(w), indexing="ij")
+            vol = _render_torch(retina, ii + mv[..., 0], jj + mv[..., 1], mv[..., 2], d, speckle, gen, device)
+        else:
+            vol = np.empty((h, w, d), dtype=np.float32)
+            srng = np.random.default_rng(seed * 7919 + (1 if name == "x" else 2))
+        for j0 in range(0, h if device is None else 0, row_chunk):
             j1 = min(h, j0 + row_chunk)
             s = tmap[j0:j1].astype(np.int64)
             mv = m[s]

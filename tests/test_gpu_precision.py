@@ -83,3 +83,40 @@ def test_solve_with_16bit_storage_tracks_float32(storage):
     rms = float(torch.sqrt(((D32 - D16) ** 2).mean()))
     print("storage %d: solution RMS vs float32 storage %.4f px" % (storage, rms))
     assert rms < 0.25
+
+
+@pytest.fixture(scope="module")
+def wide_field():
+    p, cfg = make_config("c3")
+    T, _ = true_displacement(p, cfg["w"], cfg["h"])
+    return p, cfg, T
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+def test_wide_field_precision_against_fp64(wide_field, storage):
+    # the wide-field pair (600 x 600 A-scans x 800, 10 saccades up to 25 px):
+    # kernel parity on the rounded volumes, and the storage error against the
+    # FP64 oracle on the float32 originals, at the true displacement + noise
+    import paper_2010_06931_gb300 as octmc
+    p, cfg, T = wide_field
+    D = T + np.random.default_rng(2).normal(0.0, 0.3, T.shape)
+    G = octmc.Problem(p["sx"], p["sy"], p["tx"], p["ty"], p["ax"], p["ay"], p["vx"], p["vy"], storage=storage)
+    G.set_eta(0, 0.8)
+    g = torch.empty((2, 3, cfg["h"], cfg["w"]), dtype=torch.float64, device="cuda")
+    t = G.eval_terms(0, torch.from_numpy(D).cuda(), g)
+    gn = g.cpu().numpy()
+    del G
+    Cr = O.OracleProblem(ROUND[storage](p["sx"]), ROUND[storage](p["sy"]), p["tx"], p["ty"], p["ax"], p["ay"],
+                         p["vx"], p["vy"])
+    Cr.eta = 0.8
+    fr, gr, _ = Cr.eval(D)
+    assert abs(t[4] - fr) <= 1e-5 * abs(fr)
+    assert np.linalg.norm(gn - gr) <= 1e-4 * np.linalg.norm(gr)
+    del Cr, gr
+    C = O.OracleProblem(p["sx"], p["sy"], p["tx"], p["ty"], p["ax"], p["ay"], p["vx"], p["vy"])
+    C.eta = 0.8
+    f0, g0, _ = C.eval(D)
+    ef = abs(t[4] - f0) / abs(f0)
+    eg = np.linalg.norm(gn - g0) / np.linalg.norm(g0)
+    print("wide field, storage %d: f rel err vs FP64 on float32 inputs %.2e, grad rel L2 %.2e" % (storage, ef, eg))
+    assert ef < 2e-2 and eg < 0.2
