@@ -214,6 +214,7 @@ def make_pair(w, h, d, n_layers=8, n_slabs=2, n_saccades=2, max_saccade=5.0, dri
 
     out = {}
     for name, m, tmap, sac, slow_len in (("x", mx, tx, sacx, h), ("y", my, ty, sacy, w)):
+        srng = np.random.default_rng(seed * 7919 + (1 if name == "x" else 2))
         if device is not None:
             import torch
             gen = torch.Generator(device=device)
@@ -224,7 +225,6 @@ def make_pair(w, h, d, n_layers=8, n_slabs=2, n_saccades=2, max_saccade=5.0, dri
             vol = _render_torch(retina, ii + mv[..., 0], jj + mv[..., 1], mv[..., 2], d, speckle, gen, device)
         else:
             vol = np.empty((h, w, d), dtype=np.float32)
-            srng = np.random.default_rng(seed * 7919 + (1 if name == "x" else 2))
         for j0 in range(0, h if device is None else 0, row_chunk):
             j1 = min(h, j0 + row_chunk)
             s = tmap[j0:j1].astype(np.int64)
