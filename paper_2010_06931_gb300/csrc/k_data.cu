@@ -170,64 +170,30 @@ __device__ __forceinline__ void axial(const float4& T, const float4& Tx, const f
 
 // Interpolated values (and their displacement derivatives) of one volume
 // at the lane's 4 outputs of the depth block starting at kb.
-#ifndef OCTMC_FFMA2
-#define OCTMC_FFMA2 1
-#endif
-
-// acc += (w, w) * s, two lanes of a float4 at a time (fma.rn.f32x2)
-__device__ __forceinline__ void fma4x2(float4& acc, float2 w2, const float4& s) {
-  float2 lo = __ffma2_rn(w2, make_float2(s.x, s.y), make_float2(acc.x, acc.y));
-  float2 hi = __ffma2_rn(w2, make_float2(s.z, s.w), make_float2(acc.z, acc.w));
-  acc = make_float4(lo.x, lo.y, hi.x, hi.y);
-}
-
 template <typename S>
 __device__ __forceinline__ void sample_block(const Vol& V, int kb, int lane, int dp, float I[4],
                                              float Iz[4], float Ix[4], float Iy[4]) {
   const int qk = kb + 4 * V.q + 4 * (lane - 1);  // first input depth of the lane's group
   const unsigned qc = (unsigned)(min(max(qk, 0), dp - 4) >> 2);
   float4 T = bcast(0.f), Tx = bcast(0.f), Ty = bcast(0.f);
-#if OCTMC_FFMA2
-  float2 wx2[4], dwx2[4];
-#pragma unroll
-  for (int a = 0; a < 4; a++) {
-    wx2[a] = make_float2(V.wx[a], V.wx[a]);
-    dwx2[a] = make_float2(V.dwx[a], V.dwx[a]);
-  }
-#endif
 #pragma unroll
   for (int b = 0; b < 4; b++) {
     float4 U = bcast(0.f), Ux = bcast(0.f);
 #pragma unroll
     for (int a = 0; a < 4; a++) {
       const float4 s = load4<S>(V.base, V.roff[b] + V.coff[a] + qc);
-#if OCTMC_FFMA2
-      fma4x2(U, wx2[a], s);
-      fma4x2(Ux, dwx2[a], s);
-#else
       fma4(U, V.wx[a], s);
       fma4(Ux, V.dwx[a], s);
-#endif
     }
-#if OCTMC_FFMA2
-    const float2 wy2 = make_float2(V.wy[b], V.wy[b]), dwy2 = make_float2(V.dwy[b], V.dwy[b]);
-    fma4x2(T, wy2, U);
-    fma4x2(Tx, wy2, Ux);
-    fma4x2(Ty, dwy2, U);
-#else
     fma4(T, V.wy[b], U);
     fma4(Tx, V.wy[b], Ux);
     fma4(Ty, V.dwy[b], U);
-#endif
   }
-  // groups entirely before sample 0 / after the last sample hold the edge
-  // value (warp-uniform test first: most iterations have no such group)
-  if (__any_sync(kFull, qk < 0 || qk >= dp)) {
-    if (qk < 0) {
-      T = bcast(T.x); Tx = bcast(Tx.x); Ty = bcast(Ty.x);
-    } else if (qk >= dp) {
-      T = bcast(T.w); Tx = bcast(Tx.w); Ty = bcast(Ty.w);
-    }
+  // groups entirely before sample 0 / after the last sample hold the edge value
+  if (qk < 0) {
+    T = bcast(T.x); Tx = bcast(Tx.x); Ty = bcast(Ty.x);
+  } else if (qk >= dp) {
+    T = bcast(T.w); Tx = bcast(Tx.w); Ty = bcast(Ty.w);
   }
   switch (V.r) {
     case 0: axial<0>(T, Tx, Ty, V.wz, V.dwz, I, Iz, Ix, Iy); break;
