@@ -703,3 +703,105 @@ int oracle_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------ */
+/* Final resampling and merging (Sec. 2.1, last paragraphs; Sec. 2.5).   */
+/* Readings (the paper gives no constants or formulas):                  */
+/*  - motion-corrected volume C^V = I(S^V, p_ijk + d^V_ij) (the same      */
+/*    Hermite interpolator);                                             */
+/*  - sampling density: every motion-corrected A-scan deposits weight 1   */
+/*    at its transverse sampling position (i + dx, j + dy), clamped into  */
+/*    the grid, split bilinearly over the 4 surrounding input A-scans;    */
+/*    the density of A-scan (i,j) is that map read back bilinearly at its */
+/*    own sampling position (1 without motion);                          */
+/*  - weight exp(-beta * max(0, density - 1)) ("exponentially decaying   */
+/*    for a density higher than normal"), set to 0 below tau; the two    */
+/*    volumes' weights are normalised to sum 1; where both are clipped   */
+/*    the volume with the larger weight is kept alone ("the B-scan with  */
+/*    less oversampling remains");                                       */
+/*  - en-face angiography: weights multiplied by the resampled validity  */
+/*    (Eq. 7, Sec. 2.5), normalised; 0 where both products are 0.        */
+/* ------------------------------------------------------------------ */
+static double density_at(const double *map, int w, int h, double x, double y)
+{
+    if (x < 0) x = 0;
+    if (y < 0) y = 0;
+    if (x > w - 1) x = w - 1;
+    if (y > h - 1) y = h - 1;
+    long x0 = (long)floor(x), y0 = (long)floor(y);
+    long x1 = x0 + 1 < w ? x0 + 1 : x0, y1 = y0 + 1 < h ? y0 + 1 : y0;
+    double fx = x - x0, fy = y - y0;
+    return (1 - fx) * (1 - fy) * map[y0 * w + x0] + fx * (1 - fy) * map[y0 * w + x1] +
+           (1 - fx) * fy * map[y1 * w + x0] + fx * fy * map[y1 * w + x1];
+}
+
+static void splat(double *map, int w, int h, double x, double y)
+{
+    if (x < 0) x = 0;
+    if (y < 0) y = 0;
+    if (x > w - 1) x = w - 1;
+    if (y > h - 1) y = h - 1;
+    long x0 = (long)floor(x), y0 = (long)floor(y);
+    long x1 = x0 + 1 < w ? x0 + 1 : x0, y1 = y0 + 1 < h ? y0 + 1 : y0;
+    double fx = x - x0, fy = y - y0;
+    map[y0 * w + x0] += (1 - fx) * (1 - fy);
+    map[y0 * w + x1] += fx * (1 - fy);
+    map[y1 * w + x0] += (1 - fx) * fy;
+    map[y1 * w + x1] += fx * fy;
+}
+
+/* Outputs (any may be NULL): merged[h][w][d], corrected X / Y [h][w][d],
+ * weights[2][h][w] (normalised structural weights), angio[h][w],
+ * density[2][h][w]. */
+void oracle_merge(const oracle_level *P, const double *disp, double beta, double tau, float *merged,
+                  float *cx, float *cy, float *weights, float *angio, double *density)
+{
+    const int w = P->w, h = P->h, d = P->d;
+    const long n = (long)w * h;
+    double *map = (double *)calloc((size_t)(2 * n), sizeof(double));
+    for (int V = 0; V < 2; V++)
+        for (int j = 0; j < h; j++)
+            for (int i = 0; i < w; i++)
+                splat(map + V * n, w, h, i + dget(disp, w, h, V, 0, i, j), j + dget(disp, w, h, V, 1, i, j));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int j = 0; j < h; j++)
+        for (int i = 0; i < w; i++) {
+            const long p = (long)j * w + i;
+            double wt[2], rho[2], va[2] = {1.0, 1.0};
+            for (int V = 0; V < 2; V++) {
+                double x = i + dget(disp, w, h, V, 0, i, j), y = j + dget(disp, w, h, V, 1, i, j);
+                rho[V] = density_at(map + V * n, w, h, x, y);
+                wt[V] = exp(-beta * fmax(0.0, rho[V] - 1.0));
+                if (density) density[V * n + p] = rho[V];
+            }
+            double c0 = wt[0] >= tau ? wt[0] : 0.0, c1 = wt[1] >= tau ? wt[1] : 0.0;
+            if (c0 == 0.0 && c1 == 0.0) {
+                if (wt[0] >= wt[1]) c0 = 1.0;
+                else c1 = 1.0;
+            }
+            const double wx = c0 / (c0 + c1), wy = c1 / (c0 + c1);
+            if (weights) {
+                weights[p] = (float)wx;
+                weights[n + p] = (float)wy;
+            }
+            for (int k = 0; k < d; k++) {
+                double IX = oracle_interp3(P->sx, w, h, d, i + dget(disp, w, h, 0, 0, i, j),
+                                           j + dget(disp, w, h, 0, 1, i, j), k + dget(disp, w, h, 0, 2, i, j), NULL);
+                double IY = oracle_interp3(P->sy, w, h, d, i + dget(disp, w, h, 1, 0, i, j),
+                                           j + dget(disp, w, h, 1, 1, i, j), k + dget(disp, w, h, 1, 2, i, j), NULL);
+                if (merged) merged[p * d + k] = (float)(wx * IX + wy * IY);
+                if (cx) cx[p * d + k] = (float)IX;
+                if (cy) cy[p * d + k] = (float)IY;
+            }
+            if (angio && P->ax && P->ay) {
+                double gdummy[2], AXv, AYv;
+                AXv = oracle_interp2(P->ax, w, h, i + dget(disp, w, h, 0, 0, i, j), j + dget(disp, w, h, 0, 1, i, j), gdummy);
+                AYv = oracle_interp2(P->ay, w, h, i + dget(disp, w, h, 1, 0, i, j), j + dget(disp, w, h, 1, 1, i, j), gdummy);
+                if (P->vx) va[0] = oracle_interp1(P->vx, h, j + dget(disp, w, h, 0, 1, i, j), NULL);
+                if (P->vy) va[1] = oracle_interp1(P->vy, w, i + dget(disp, w, h, 1, 0, i, j), NULL);
+                double a0 = fmax(0.0, c0 * va[0]), a1 = fmax(0.0, c1 * va[1]);
+                angio[p] = (a0 + a1 > 0) ? (float)((a0 * AXv + a1 * AYv) / (a0 + a1)) : 0.0f;
+            }
+        }
+    free(map);
+}

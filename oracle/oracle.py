@@ -91,6 +91,7 @@ def _load():
                                            C.POINTER(_Stats)]
         lib.oracle_solve_level.restype = C.c_int
         lib.oracle_num_threads.restype = C.c_int
+        lib.oracle_merge.argtypes = [C.POINTER(_Level), _dp, C.c_double, C.c_double] + [C.c_void_p] * 5 + [C.c_void_p]
         _lib = lib
     return _lib
 
@@ -276,6 +277,23 @@ class OracleProblem:
         st = _Stats()
         _load().oracle_solve_level(C.byref(L), x, C.byref(opt), C.byref(st))
         return x, dict(iters=st.iters, evals=st.evals, status=st.status, f=st.f, eta=self.eta)
+
+    def merge(self, disp, beta=2.0, tau=0.05):
+        """Final resampling and merging (Sec. 2.1, 2.5): dict with merged, cx, cy
+        [h][w][d], weights [2][h][w], angio [h][w] (if angiography), density [2][h][w]."""
+        disp = np.ascontiguousarray(disp, dtype=np.float64)
+        h, w, d = self.h, self.w, self.d
+        out = dict(merged=np.zeros((h, w, d), np.float32), cx=np.zeros((h, w, d), np.float32),
+                   cy=np.zeros((h, w, d), np.float32), weights=np.zeros((2, h, w), np.float32),
+                   angio=np.zeros((h, w), np.float32), density=np.zeros((2, h, w)))
+        L = self._level()
+        _load().oracle_merge(C.byref(L), disp, float(beta), float(tau), out["merged"].ctypes.data,
+                             out["cx"].ctypes.data, out["cy"].ctypes.data, out["weights"].ctypes.data,
+                             out["angio"].ctypes.data if self.ax is not None else None,
+                             out["density"].ctypes.data)
+        if self.ax is None:
+            out["angio"] = None
+        return out
 
     def downsample(self):
         """The next coarser pyramid level (Sec. 2.1, factor 2)."""
