@@ -145,6 +145,29 @@ int octmc_solve_full(octmc_problem *p, double *disp_out_dev, octmc_stats *st);
  * grid with clamped coordinates. */
 int octmc_prolong(octmc_problem *p, int level, const double *coarse_dev, double *fine_dev);
 
+/* Final resampling and merging at level 0 (Sec. 2.1 last paragraphs,
+ * Sec. 2.5) for the level-0 device field disp0_dev ([2][3][h][w] float64):
+ *   corrected_x / corrected_y (device float32 [h][w][d]): each scan resampled
+ *     at p_ijk + d^V_ij with the objective's interpolator;
+ *   weights (device float32 [2][h][w]): normalised per-A-scan merge weights.
+ *     The sampling density of scan V is the map of the positions
+ *     (i + dx^V, j + dy^V) (clamped into the grid) splatted bilinearly with
+ *     weight 1, read back bilinearly at A-scan (i, j)'s own position; the raw
+ *     weight is exp(-beta * max(0, density - 1)), weights below tau are set
+ *     to 0, the pair is normalised to sum 1, and where both were clipped the
+ *     scan with the larger raw weight is kept alone;
+ *   merged (device float32 [h][w][d]): wX C^X + wY C^Y;
+ *   angio (device float32 [h][w]): en-face angiography images resampled at
+ *     the displaced transverse positions, merged with the clipped raw
+ *     weights times the resampled validity (Eq. 7), 0 where both are 0.
+ * Any output may be NULL.  The density map is accumulated in 64-bit
+ * fixed point (2^-32 units), so the result is deterministic.  Typical
+ * beta = 2, tau = 0.05.  Errors: INVALID_ARG (beta < 0, tau outside [0, 1]),
+ * OOM (first call allocates 16 w h bytes of density maps kept by the
+ * problem), CUDA. */
+int octmc_merge(octmc_problem *p, const double *disp0_dev, double beta, double tau, float *merged,
+                float *corrected_x, float *corrected_y, float *weights, float *angio);
+
 /* Copies pyramid data of `level` to device buffers (any may be NULL):
  * sx/sy as float32 [h][w][d], ax/ay [h][w], vx[h], vy[w]. */
 int octmc_level_data(const octmc_problem *p, int level, float *sx, float *sy, float *ax, float *ay,

@@ -179,6 +179,23 @@ class Problem:
                 "octmc_level_data")
         return out
 
+    def merge(self, disp0, beta=2.0, tau=0.05, outputs=("merged", "weights", "angio")):
+        """``octmc_merge``: final resampling and merging at level 0 (Sec. 2.1, 2.5).
+
+        ``outputs`` picks any of "merged", "corrected_x", "corrected_y",
+        "weights", "angio"; returns a dict of float32 device tensors."""
+        _check_disp(disp0, self.disp_shape(0))
+        w, h, d = self.level_shape(0)
+        shapes = {"merged": (h, w, d), "corrected_x": (h, w, d), "corrected_y": (h, w, d), "weights": (2, h, w),
+                  "angio": (h, w)}
+        unknown = set(outputs) - set(shapes)
+        if unknown:
+            raise ValueError("unknown merge outputs %s" % sorted(unknown))
+        out = {k: torch.empty(shapes[k], dtype=torch.float32, device="cuda") for k in outputs}
+        N.check(N.lib().octmc_merge(self._h, _ptr(disp0), float(beta), float(tau),
+                                    *[_ptr(out.get(k)) for k in ("merged", "corrected_x", "corrected_y", "weights",
+                                                                 "angio")]), "octmc_merge")
+        return out
 
     # -- kernel timing
     def profile_enable(self, enable=True):

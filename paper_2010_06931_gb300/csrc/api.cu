@@ -336,6 +336,7 @@ struct octmc_problem {
   double* gb = nullptr;
   double* dir = nullptr;
   octmc_lbfgs* opt = nullptr;
+  unsigned long long* mcounts = nullptr;  // merge: fixed-point density maps [2][h][w]
   std::vector<void*> temps;  // float32 pyramid copies while building 16-bit storage
   // optional CUDA-event timing of the data-term kernel (octmc_profile_*)
   bool profile = false;
@@ -358,6 +359,7 @@ struct octmc_problem {
     dfree(str); dfree(ang); dfree(gdata); dfree(partials); dfree(counters); dfree(res);
     if (res_host) cudaFreeHost(res_host);
     dfree(x); dfree(g); dfree(xt); dfree(gt); dfree(xb); dfree(gb); dfree(dir);
+    dfree(mcounts);
     delete opt;
   }
 
@@ -1134,6 +1136,24 @@ int octmc_solve_full(octmc_problem* p, double* disp_out, octmc_stats* st) {
     if (st)
       for (size_t k = 0; k < M.stats.size(); k++) st[k] = M.stats[k];
     return rc;
+  });
+}
+
+int octmc_merge(octmc_problem* p, const double* disp0, double beta, double tau, float* merged, float* cx,
+                float* cy, float* weights, float* angio) {
+  if (!valid_level(p, 0) || !disp0 || !(beta >= 0) || !std::isfinite(beta) || !(tau >= 0) || !(tau <= 1))
+    return OCTMC_ERR_INVALID_ARG;
+  return guarded([&] {
+    const LevelDev& L = p->lv[0].dev;
+    float* wts = weights;
+    if (merged || weights || angio) {
+      if (!p->mcounts) p->mcounts = dalloc<unsigned long long>(2 * (size_t)p->plane(0));
+      if (!wts && merged) wts = p->gdata;  // scratch of 6 w h floats, unused outside evaluations
+      CK(launch_merge_weights(L, disp0, beta, tau, p->mcounts, wts, angio, p->st));
+    }
+    if (merged || cx || cy) CK(launch_resample_merge(L, disp0, wts, merged, cx, cy, p->st));
+    CK(cudaStreamSynchronize(p->st));
+    return OCTMC_OK;
   });
 }
 

@@ -245,6 +245,12 @@ cudaError_t launch_reg(const RegArgs& a, cudaStream_t s);
 int reg_grid_blocks(int64_t n_ascans);
 int msum_grid_blocks();
 
+// Final resampling / merging (Sec. 2.1, 2.5).
+cudaError_t launch_resample_merge(const LevelDev& L, const double* disp, const float* weights, float* merged,
+                                  float* cx, float* cy, cudaStream_t s);
+cudaError_t launch_merge_weights(const LevelDev& L, const double* disp, double beta, double tau,
+                                 unsigned long long* counts, float* weights, float* angio, cudaStream_t s);
+
 cudaError_t launch_pad_depth(float* vol, int64_t columns, int d, int dp, cudaStream_t s);
 cudaError_t launch_pyr_volume(const float* in, int w, int h, int d, int dp, float* out, int w2,
                               int h2, int d2, int dp2, cudaStream_t s);

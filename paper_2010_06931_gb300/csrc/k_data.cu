@@ -370,7 +370,59 @@ data_multi_kernel(const __grid_constant__ DataMulti M) {
   data_ascan<T>(A, p, threadIdx.x & 31);
 }
 
+// Motion-corrected resampling and merging of one A-scan (warp): both scans
+// resampled along depth at the displaced positions (the derivative parts of
+// sample_block are dead code here), merged with the per-A-scan weights.
+template <typename T>
+__global__ void __launch_bounds__(kWarpsPerBlock * kWarp, OCTMC_DATA_MINB)
+resample_merge_kernel(const LevelDev L, const double* __restrict__ disp, const float* __restrict__ weights,
+                      float* merged, float* cx, float* cy) {
+  const int64_t nasc = (int64_t)L.w * L.h;
+  const int64_t p = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (p >= nasc) return;
+  const int lane = threadIdx.x & 31;
+  const int i = (int)(p % L.w), j = (int)(p / L.w);
+  int base[6];
+  float frac[6];
+  split_displacement(disp, nasc, p, i, j, L, lane, base, frac);
+  Vol VX, VY;
+  setup_vol(VX, L.sx, L, base, frac);
+  setup_vol(VY, L.sy, L, base + 3, frac + 3);
+  const float wx = weights ? weights[p] : 0.5f, wy = weights ? weights[nasc + p] : 0.5f;
+  for (int kb = 0; kb < L.d; kb += kOutPerIter) {
+    float IX[4], IzX[4], IxX[4], IyX[4], IY[4], IzY[4], IxY[4], IyY[4];
+    sample_block<T>(VX, kb, lane, L.dp, IX, IzX, IxX, IyX);
+    sample_block<T>(VY, kb, lane, L.dp, IY, IzY, IxY, IyY);
+    if (lane >= 1 && lane <= kOutLanes) {
+#pragma unroll
+      for (int o = 0; o < 4; o++) {
+        const int k = kb + 4 * (lane - 1) + o;
+        if (k < L.d) {
+          const int64_t e = p * L.d + k;
+          if (merged) merged[e] = fmaf(wx, IX[o], wy * IY[o]);
+          if (cx) cx[e] = IX[o];
+          if (cy) cy[e] = IY[o];
+        }
+      }
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_resample_merge(const LevelDev& L, const double* disp, const float* weights, float* merged,
+                                  float* cx, float* cy, cudaStream_t s) {
+  const int64_t nasc = (int64_t)L.w * L.h;
+  const int64_t blocks = (nasc + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  if (blocks <= 0) return cudaSuccess;
+  if (L.dtype == OCTMC_BF16)
+    resample_merge_kernel<__nv_bfloat16><<<(unsigned)blocks, kWarpsPerBlock * kWarp, 0, s>>>(L, disp, weights, merged, cx, cy);
+  else if (L.dtype == OCTMC_F16)
+    resample_merge_kernel<__half><<<(unsigned)blocks, kWarpsPerBlock * kWarp, 0, s>>>(L, disp, weights, merged, cx, cy);
+  else
+    resample_merge_kernel<float><<<(unsigned)blocks, kWarpsPerBlock * kWarp, 0, s>>>(L, disp, weights, merged, cx, cy);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_data_multi(const DataMulti& M, int dtype, cudaStream_t s) {
   if (M.nslots <= 0) return cudaSuccess;
