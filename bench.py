@@ -45,6 +45,16 @@ def bytes_per_eval(w, h, d, s=4):
     return float(w) * h * (2 * d * s + 2 * 4 + 6 * 8 + 8 * 4)
 
 
+def merge_bytes(w, h, d, s=4):
+    """Algorithmic bytes of one final resampling + merge: both volumes read
+    once, the merged volume written once, the displacement field read twice
+    (weights, resampling), density maps (64-bit, 2 planes) cleared, splatted
+    and read, weights written and read, angio images read, merged angio
+    written."""
+    n = w * h
+    return n * (2 * d * s + d * 4 + 2 * 48 + 3 * 16 + 2 * 8 + 8 + 4)
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -133,6 +143,14 @@ def measured_peaks():
         return {}
 
 
+def data_kernel_sha1():
+    """sha1 over the sources that define the data-term kernel."""
+    hsh = hashlib.sha1()
+    for f in ("common.cuh", "sample.cuh", "k_data.cu"):
+        hsh.update(open(os.path.join(ROOT, "paper_2010_06931_gb300", "csrc", f), "rb").read())
+    return hsh.hexdigest()
+
+
 def kernel_traffic(w, h, d):
     """dram bytes per launch of the data-term kernel from the committed ncu
     summary, scaled to this workload; None if the kernel source changed."""
@@ -141,8 +159,7 @@ def kernel_traffic(w, h, d):
         rec = json.load(open(path))
     except Exception:
         return None
-    src = open(os.path.join(ROOT, "paper_2010_06931_gb300", "csrc", "k_data.cu"), "rb").read()
-    if rec.get("k_data_sha1") != hashlib.sha1(src).hexdigest():
+    if rec.get("src_sha1") != data_kernel_sha1():
         return None
     scale = (w * h * d) / float(rec["w"] * rec["h"] * rec["d"])
     return rec["dram_bytes_per_launch"] * scale
@@ -293,6 +310,23 @@ def run_ours(args):
                  "evals": int(sum(s["evals"] for s in stats)), "iters": [s["iters"] for s in stats],
                  "status": [s["status"] for s in stats]}
 
+    # ---- final resampling + merging of the pair (level 0, at the solution or the true field)
+    Dm = out if solve is not None else D
+    mo = P.merge(Dm, outputs=("merged", "weights", "angio"))
+    for _ in range(3):
+        P.merge(Dm, out=mo, outputs=tuple(mo))
+    barrier()
+    e0.record(stream)
+    n_merge = 10
+    for _ in range(n_merge):
+        P.merge(Dm, out=mo, outputs=tuple(mo))
+    e1.record(stream)
+    barrier()
+    merge_ms = e0.elapsed_time(e1) / n_merge
+    mb = merge_bytes(w, h, d)
+    merge = {"ms": merge_ms, "bytes": mb, "gbs": mb / merge_ms / 1e6, "outputs": list(mo),
+             "note": "weights (density splat + gather) and resample-merge kernels, one host sync per call"}
+
     # max over ranks
     t = torch.tensor([ms, ms_e2e], dtype=torch.float64, device="cuda")
     if dist is not None:
@@ -305,6 +339,7 @@ def run_ours(args):
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     alu_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    merge["hbm_frac"] = merge["gbs"] / hbm_peak
     kavg = kern_ms / max(kern_n, 1) / 1e3
     F = flops_per_eval(w, h, d)
     B = bytes_per_eval(w, h, d)
@@ -329,6 +364,7 @@ def run_ours(args):
         "gpu_launches": 3 * args.steps,
         "clocks": clk,
         "solve": solve,
+        "merge": merge,
     }
     if not args.no_cpu and ws == 1:
         line["cpu_baseline"] = cpu_baseline(pair, cfg)

@@ -179,11 +179,12 @@ class Problem:
                 "octmc_level_data")
         return out
 
-    def merge(self, disp0, beta=2.0, tau=0.05, outputs=("merged", "weights", "angio")):
+    def merge(self, disp0, beta=2.0, tau=0.05, outputs=("merged", "weights", "angio"), out=None):
         """``octmc_merge``: final resampling and merging at level 0 (Sec. 2.1, 2.5).
 
         ``outputs`` picks any of "merged", "corrected_x", "corrected_y",
-        "weights", "angio"; returns a dict of float32 device tensors."""
+        "weights", "angio"; returns a dict of float32 device tensors (those of
+        ``out`` when given, a dict returned by an earlier call)."""
         _check_disp(disp0, self.disp_shape(0))
         w, h, d = self.level_shape(0)
         shapes = {"merged": (h, w, d), "corrected_x": (h, w, d), "corrected_y": (h, w, d), "weights": (2, h, w),
@@ -191,7 +192,14 @@ class Problem:
         unknown = set(outputs) - set(shapes)
         if unknown:
             raise ValueError("unknown merge outputs %s" % sorted(unknown))
-        out = {k: torch.empty(shapes[k], dtype=torch.float32, device="cuda") for k in outputs}
+        if out is None:
+            out = {k: torch.empty(shapes[k], dtype=torch.float32, device="cuda") for k in outputs}
+        else:
+            out = {k: out[k] for k in outputs}
+            for k, t in out.items():
+                if tuple(t.shape) != shapes[k] or t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+                    raise ValueError("merge output %s must be a contiguous float32 CUDA tensor of shape %s"
+                                     % (k, shapes[k]))
         N.check(N.lib().octmc_merge(self._h, _ptr(disp0), float(beta), float(tau),
                                     *[_ptr(out.get(k)) for k in ("merged", "corrected_x", "corrected_y", "weights",
                                                                  "angio")]), "octmc_merge")

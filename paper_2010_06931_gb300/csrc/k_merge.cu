@@ -8,6 +8,7 @@
 // (weights in units of 2^-32), so its value does not depend on the order of
 // the additions.
 #include "common.cuh"
+#include "sample.cuh"
 
 namespace octmc {
 namespace {
@@ -106,6 +107,56 @@ __global__ void weights_kernel(LevelDev L, const double* __restrict__ disp, floa
   }
 }
 
+// Motion-corrected resampling and merging of one A-scan (warp): both scans
+// resampled along depth at the displaced positions (the derivative parts of
+// sample_block are dead code here), merged with the per-A-scan weights.
+// Forward only, so it fits in 40 registers: 6 blocks (48 warps) per SM keep
+// more loads in flight than the data kernel's 3.  vec4: d % 4 == 0 and every
+// output 16-byte aligned, so a lane's 4 outputs go out as one 128-bit store.
+template <typename T>
+__global__ void __launch_bounds__(kWarpsPerBlock * kWarp, 6)
+resample_merge_kernel(const LevelDev L, const double* __restrict__ disp, const float* __restrict__ weights,
+                      float* merged, float* cx, float* cy, bool vec4) {
+  const int64_t nasc = (int64_t)L.w * L.h;
+  const int64_t p = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (p >= nasc) return;
+  const int lane = threadIdx.x & 31;
+  const int i = (int)(p % L.w), j = (int)(p / L.w);
+  int base[6];
+  float frac[6];
+  split_displacement(disp, nasc, p, i, j, L, lane, base, frac);
+  Vol VX, VY;
+  setup_vol(VX, L.sx, L, base, frac);
+  setup_vol(VY, L.sy, L, base + 3, frac + 3);
+  const float wx = weights ? weights[p] : 0.5f, wy = weights ? weights[nasc + p] : 0.5f;
+  for (int kb = 0; kb < L.d; kb += kOutPerIter) {
+    float IX[4], IzX[4], IxX[4], IyX[4], IY[4], IzY[4], IxY[4], IyY[4];
+    sample_block<T>(VX, kb, lane, L.dp, IX, IzX, IxX, IyX);
+    sample_block<T>(VY, kb, lane, L.dp, IY, IzY, IxY, IyY);
+    const int k0 = kb + 4 * (lane - 1);
+    if (lane >= 1 && lane <= kOutLanes && k0 < L.d) {
+      const int64_t e0 = p * L.d + k0;
+      if (vec4) {  // k0 + 3 < d as d % 4 == 0
+        if (merged)
+          *reinterpret_cast<float4*>(merged + e0) =
+              make_float4(fmaf(wx, IX[0], wy * IY[0]), fmaf(wx, IX[1], wy * IY[1]), fmaf(wx, IX[2], wy * IY[2]),
+                          fmaf(wx, IX[3], wy * IY[3]));
+        if (cx) *reinterpret_cast<float4*>(cx + e0) = make_float4(IX[0], IX[1], IX[2], IX[3]);
+        if (cy) *reinterpret_cast<float4*>(cy + e0) = make_float4(IY[0], IY[1], IY[2], IY[3]);
+      } else {
+#pragma unroll
+        for (int o = 0; o < 4; o++) {
+          if (k0 + o < L.d) {
+            if (merged) merged[e0 + o] = fmaf(wx, IX[o], wy * IY[o]);
+            if (cx) cx[e0 + o] = IX[o];
+            if (cy) cy[e0 + o] = IY[o];
+          }
+        }
+      }
+    }
+  }
+}
+
 inline unsigned grid_for(int64_t n) {
   int64_t b = (n + kThreads - 1) / kThreads;
   if (b < 1) b = 1;
@@ -114,6 +165,23 @@ inline unsigned grid_for(int64_t n) {
 }
 
 }  // namespace
+
+cudaError_t launch_resample_merge(const LevelDev& L, const double* disp, const float* weights, float* merged,
+                                  float* cx, float* cy, cudaStream_t s) {
+  const int64_t nasc = (int64_t)L.w * L.h;
+  const int64_t blocks = (nasc + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  if (blocks <= 0) return cudaSuccess;
+  auto a16 = [](const float* q) { return ((uintptr_t)q & 15u) == 0; };
+  const bool vec4 = (L.d % 4 == 0) && a16(merged) && a16(cx) && a16(cy);
+  const unsigned threads = kWarpsPerBlock * kWarp;
+  if (L.dtype == OCTMC_BF16)
+    resample_merge_kernel<__nv_bfloat16><<<(unsigned)blocks, threads, 0, s>>>(L, disp, weights, merged, cx, cy, vec4);
+  else if (L.dtype == OCTMC_F16)
+    resample_merge_kernel<__half><<<(unsigned)blocks, threads, 0, s>>>(L, disp, weights, merged, cx, cy, vec4);
+  else
+    resample_merge_kernel<float><<<(unsigned)blocks, threads, 0, s>>>(L, disp, weights, merged, cx, cy, vec4);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_merge_weights(const LevelDev& L, const double* disp, double beta, double tau,
                                  unsigned long long* counts, float* weights, float* angio, cudaStream_t s) {
