@@ -22,8 +22,13 @@ in for them with the same structure:
 * sampling-time maps: raster order with a flyback of 25 % of a B-scan
   (500 x 500 x 5 repeats at 400 kHz take about 3.9 s, Sec. 3.3).
 
+``make_octa_scan`` renders one scan's 3-D angiography (amplitude
+decorrelation) and OCT volumes for the saccade detection and en-face
+projection steps (Sec. 2.2, 2.3).
+
 All arrays are in the common frame: volumes ``[h][w][d]`` (depth contiguous),
 images and time maps ``[h][w]``; ``vx`` has one value per row (the X-fast
 scan's B-scans are rows), ``vy`` one per column.
 """
 from .generator import CONFIGS, make_pair, make_config, true_displacement  # noqa: F401
+from .octa import make_octa_scan  # noqa: F401

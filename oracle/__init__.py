@@ -5,13 +5,16 @@ against.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
 leg of ``bench.py`` may import this package.  It shares no code with the
 CUDA library in ``paper_2010_06931_gb300``.
 
-The arithmetic lives in ``octmc_oracle.c`` (plain C, double precision);
-this module compiles it on demand, loads it with ctypes and adds the
-multi-resolution driver (pyramid -> per-level eta -> L-BFGS -> prolongation),
-Sec. 2.1 of Ploner et al. (arXiv 2010.06931).
+The arithmetic lives in ``octmc_oracle.c`` (the objective, its gradient, the
+pyramid, L-BFGS and the final merge) and ``octa_oracle.c`` (saccade
+validity and the en-face OCTA projection, Sec. 2.2-2.3), plain C in double
+precision; this module compiles them on demand, loads them with ctypes and
+adds the multi-resolution driver (pyramid -> per-level eta -> L-BFGS ->
+prolongation), Sec. 2.1 of Ploner et al. (arXiv 2010.06931).
 """
 from .oracle import (  # noqa: F401
     OracleProblem, build, cr_weights, interp1, interp2, interp3, loss, chain,
     pyramid_volume, pyramid_image, pyramid_line, pyramid_time, prolong,
     lbfgs_direction, num_threads, LOSS_PSEUDO_HUBER, LOSS_SSD,
+    saccade_validity, median3, rank_filter, percentile, bscan_median_subtract, replace_invalid, enface,
 )

@@ -13,7 +13,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "octmc_oracle.c")
+_SRCS = [os.path.join(_HERE, "octmc_oracle.c"), os.path.join(_HERE, "octa_oracle.c")]
 _LIB = os.path.join(_HERE, "liboctmc_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -50,11 +50,11 @@ class _Stats(C.Structure):
 def build(force=False):
     """Compile the oracle shared library (gcc, OpenMP) if it is missing or stale."""
     with _lock:
-        stale = (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)
+        stale = (not os.path.exists(_LIB)) or any(os.path.getmtime(_LIB) < os.path.getmtime(s) for s in _SRCS)
         if force or stale:
             tmp = _LIB + ".tmp%d" % os.getpid()
             subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11",
-                                   "-o", tmp, _SRC, "-lm"])
+                                   "-o", tmp] + _SRCS + ["-lm"])
             os.replace(tmp, _LIB)
     return _LIB
 
@@ -92,6 +92,15 @@ def _load():
         lib.oracle_solve_level.restype = C.c_int
         lib.oracle_num_threads.restype = C.c_int
         lib.oracle_merge.argtypes = [C.POINTER(_Level), _dp, C.c_double, C.c_double] + [C.c_void_p] * 5 + [C.c_void_p]
+        lib.oracle_saccade_validity.argtypes = [_fp, C.c_int, C.c_int, C.c_int, C.c_int, _fp, _dp]
+        lib.oracle_median3.argtypes = [_fp, C.c_int, C.c_int, C.c_int, _fp]
+        lib.oracle_rank_filter.argtypes = [_fp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _fp]
+        lib.oracle_percentile.argtypes = [_fp, C.c_long, C.c_double]
+        lib.oracle_percentile.restype = C.c_double
+        lib.oracle_bscan_median_subtract.argtypes = [_fp, C.c_int, C.c_int, C.c_int]
+        lib.oracle_replace_invalid.argtypes = [_fp, C.c_int, C.c_int, C.c_int, _fp]
+        lib.oracle_enface.argtypes = [_fp, _fp, C.c_int, C.c_int, C.c_int, C.c_int, _fp, C.c_double, C.c_double,
+                                      C.c_double, C.c_double, C.c_void_p, _fp, _dp]
         _lib = lib
     return _lib
 
@@ -328,3 +337,70 @@ class OracleProblem:
             st["level"] = lv
             stats.append(st)
         return disp, stats
+
+
+# ---------------------------------------------------------------- angiography preprocessing (Sec. 2.2, 2.3)
+def _vol(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def saccade_validity(A, fast_axis):
+    """(validity per B-scan float32, mean decorrelation per B-scan float64) of an
+    OCTA volume [h][w][d]; fast_axis 0 (X-fast, B-scans are rows) or 1."""
+    A = _vol(A)
+    h, w, d = A.shape
+    nb = h if fast_axis == 0 else w
+    v = np.zeros(nb, np.float32)
+    m = np.zeros(nb)
+    _load().oracle_saccade_validity(A, w, h, d, int(fast_axis), v, m)
+    return v, m
+
+
+def median3(A):
+    A = _vol(A)
+    out = np.empty_like(A)
+    h, w, d = A.shape
+    _load().oracle_median3(A, w, h, d, out)
+    return out
+
+
+def rank_filter(A, axis, width=15, rank=3):
+    """rank-th smallest (1-based) of `width` samples along axis 0 (x) or 1 (y)."""
+    A = _vol(A)
+    out = np.empty_like(A)
+    h, w, d = A.shape
+    _load().oracle_rank_filter(A, w, h, d, int(axis), int(width), int(rank), out)
+    return out
+
+
+def percentile(x, q):
+    x = _vol(np.ravel(x))
+    return _load().oracle_percentile(x, x.size, float(q))
+
+
+def bscan_median_subtract(E, fast_axis):
+    E = _vol(E).copy()
+    h, w = E.shape
+    _load().oracle_bscan_median_subtract(E, w, h, int(fast_axis))
+    return E
+
+
+def replace_invalid(E, fast_axis, v):
+    E = _vol(E).copy()
+    h, w = E.shape
+    _load().oracle_replace_invalid(E, w, h, int(fast_axis), _vol(v))
+    return E
+
+
+def enface(A, S, fast_axis, v, q_lo=0.05, q_hi=0.95, thresh=0.1, t_oct=None, want_filtered=False):
+    """En-face OCTA image of one scan (Sec. 2.3).  Returns (E [h][w], info dict,
+    rank-filtered volume or None)."""
+    A, S = _vol(A), _vol(S)
+    h, w, d = A.shape
+    E = np.zeros((h, w), np.float32)
+    info = np.zeros(4)
+    filt = np.empty_like(A) if want_filtered else None
+    _load().oracle_enface(A, S, w, h, d, int(fast_axis), _vol(v), float(q_lo), float(q_hi), float(thresh),
+                          float("nan") if t_oct is None else float(t_oct),
+                          None if filt is None else filt.ctypes.data, E, info)
+    return E, dict(p_lo=info[0], p_hi=info[1], t_oct=info[2], kept=int(info[3])), filt
