@@ -168,6 +168,43 @@ int octmc_prolong(octmc_problem *p, int level, const double *coarse_dev, double 
 int octmc_merge(octmc_problem *p, const double *disp0_dev, double beta, double tau, float *merged,
                 float *corrected_x, float *corrected_y, float *weights, float *angio);
 
+/* ---------------------------------------------------------------------
+ * Angiography preprocessing of one scan (inputs of the objective).
+ * Volumes are device float32 [h][w][d] (depth contiguous) on the common
+ * grid; fast_axis 0: X-fast scan, B-scans are the rows j (h of them);
+ * fast_axis 1: Y-fast scan, B-scans are the columns i (w of them).
+ * stream: a cudaStream_t (NULL: the legacy default stream).  Both calls
+ * synchronise the stream before returning; scratch comes from the
+ * stream-ordered allocator and is released before returning.
+ * --------------------------------------------------------------------- */
+
+/* Saccade validity (Sec. 2.2): m_b = mean of the OCTA volume over B-scan b;
+ * B-scan b is saturated if m_b > mu + 3 sigma (mean and population standard
+ * deviation of the m_b); v_dev[b] (device, one float per B-scan) is 0 if b
+ * or a B-scan within 2 of it is saturated, else 1.  means_dev (device, may
+ * be NULL) receives the m_b (float64).  Errors: INVALID_ARG, CUDA. */
+int octmc_saccade_validity(const float *octa_dev, int w, int h, int d, int fast_axis, float *v_dev,
+                           double *means_dev, void *stream);
+
+/* En-face OCTA image (Sec. 2.3): 3x3x3 median of the OCTA volume, then the
+ * 3rd smallest of 15 samples along the fast axis, then along the slow axis
+ * (edges replicated); the q_lo / q_hi quantiles (linear interpolation between
+ * order statistics) of the filtered voxels of the valid B-scans (all if none
+ * is valid) map to 0 / 1 and voxels below `thresh` form the lateral-contrast
+ * mask; voxels whose OCT value exceeds t_oct (NaN: the mean OCT value over
+ * the valid B-scans) form the OCT mask.  enface_dev [h][w] receives the depth
+ * mean of the OCTA voxels in both masks (0 where none), minus the median of
+ * its B-scan, with invalid B-scans (v_dev == 0) replaced by the nearest valid
+ * one (lower index on a tie).  filtered_dev (device [h][w][d], may be NULL)
+ * receives the rank-filtered volume; info_host (may be NULL) receives
+ * [q_lo quantile, q_hi quantile, t_oct, voxels in both masks].  The paper
+ * uses q_lo = 0.05, q_hi = 0.95, thresh = 0.1.  Inputs must be finite.
+ * Errors: INVALID_ARG, UNSUPPORTED (more than 4096 A-scans per B-scan), OOM,
+ * CUDA. */
+int octmc_enface(const float *octa_dev, const float *oct_dev, int w, int h, int d, int fast_axis,
+                 const float *v_dev, double q_lo, double q_hi, double thresh, double t_oct, float *enface_dev,
+                 float *filtered_dev, double *info_host, void *stream);
+
 /* Copies pyramid data of `level` to device buffers (any may be NULL):
  * sx/sy as float32 [h][w][d], ax/ay [h][w], vx[h], vy[w]. */
 int octmc_level_data(const octmc_problem *p, int level, float *sx, float *sy, float *ax, float *ay,

@@ -216,6 +216,50 @@ class Problem:
         return ms.value, n.value
 
 
+def _fvol(a, ndim):
+    t = _as_tensor(a, torch.float32, "cuda")
+    if t.dim() != ndim or not t.is_contiguous():
+        raise ValueError("expected a contiguous %d-d float32 array" % ndim)
+    return t
+
+
+def saccade_validity(octa, fast_axis):
+    """``octmc_saccade_validity`` (Sec. 2.2): (validity per B-scan float32,
+    mean decorrelation per B-scan float64) of an OCTA volume [h][w][d];
+    fast_axis 0 for an X-fast scan (B-scans are rows), 1 for Y-fast."""
+    A = _fvol(octa, 3)
+    h, w, d = A.shape
+    nb = h if fast_axis == 0 else w
+    v = torch.empty(nb, dtype=torch.float32, device="cuda")
+    m = torch.empty(nb, dtype=torch.float64, device="cuda")
+    N.check(N.lib().octmc_saccade_validity(_ptr(A), w, h, d, int(fast_axis), _ptr(v), _ptr(m), _stream_ptr()),
+            "octmc_saccade_validity")
+    return v, m
+
+
+def enface(octa, oct, fast_axis, v, q_lo=0.05, q_hi=0.95, thresh=0.1, t_oct=None, out=None, filtered=None):
+    """``octmc_enface`` (Sec. 2.3): the en-face OCTA image [h][w] of one scan.
+    Returns (image, info dict with the two quantiles, the OCT threshold and
+    the voxels kept).  ``filtered`` (optional [h][w][d] float32 CUDA tensor)
+    receives the rank-filtered volume."""
+    A, S = _fvol(octa, 3), _fvol(oct, 3)
+    if A.shape != S.shape:
+        raise ValueError("OCTA and OCT volumes differ in shape")
+    h, w, d = A.shape
+    vv = _fvol(v, 1)
+    if vv.numel() != (h if fast_axis == 0 else w):
+        raise ValueError("validity needs one value per B-scan")
+    E = out if out is not None else torch.empty((h, w), dtype=torch.float32, device="cuda")
+    if filtered is not None and (tuple(filtered.shape) != (h, w, d) or filtered.dtype != torch.float32
+                                 or not filtered.is_cuda or not filtered.is_contiguous()):
+        raise ValueError("filtered must be a contiguous float32 CUDA tensor of the volume's shape")
+    info = (C.c_double * 4)()
+    N.check(N.lib().octmc_enface(_ptr(A), _ptr(S), w, h, d, int(fast_axis), _ptr(vv), float(q_lo), float(q_hi),
+                                 float(thresh), float("nan") if t_oct is None else float(t_oct), _ptr(E),
+                                 _ptr(filtered), info, _stream_ptr()), "octmc_enface")
+    return E, dict(p_lo=info[0], p_hi=info[1], t_oct=info[2], kept=int(info[3]))
+
+
 def create_problem(*args, **kw):
     """``octmc_create_problem``: see :class:`Problem`."""
     return Problem(*args, **kw)

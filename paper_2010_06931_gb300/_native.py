@@ -54,6 +54,9 @@ _SIGS = {
     "octmc_prolong": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "octmc_level_data": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 6),
     "octmc_merge": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double] + [C.c_void_p] * 5),
+    "octmc_saccade_validity": (C.c_int, [C.c_void_p] + [C.c_int] * 4 + [C.c_void_p] * 3),
+    "octmc_enface": (C.c_int, [C.c_void_p, C.c_void_p] + [C.c_int] * 4 + [C.c_void_p] + [C.c_double] * 4
+                     + [C.c_void_p] * 4),
     "octmc_lbfgs_create": (C.c_int, [C.c_int64, C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]),
     "octmc_lbfgs_destroy": (None, [C.c_void_p]),
     "octmc_lbfgs_push": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),

@@ -1,0 +1,538 @@
+// Angiography preprocessing of one scan (Ploner et al., Sec. 2.2 and 2.3):
+// saccade validity of the B-scans and the en-face OCTA projection.
+//
+//   bscan_sum_kernel     per-B-scan sums (every sample widened exactly and
+//                        added in float64, fixed tree per block): mean
+//                        decorrelation of each B-scan, and the OCT sums for
+//                        the OCT threshold
+//   validity_kernel      mu, sigma of the B-scan means, the 3-sigma test and
+//                        the +-2 B-scan dilation (one block, float64)
+//   median3_kernel       3x3x3 median per voxel (edge replicated) by
+//                        forgetful selection: 15 candidates, repeatedly drop
+//                        the minimum and maximum and take in the next sample
+//   rank15_kernel        3rd smallest of 15 samples along x or y (edge
+//                        replicated) with a 3-deep insertion network
+//   radix_hist_kernel /  exact order statistics of the filtered voxels of the
+//   radix_pick_kernel    valid B-scans by 3 passes of 11-bit (last 10-bit)
+//                        radix selection on order-preserving integer keys
+//                        (integer histograms: deterministic)
+//   finish_kernel        percentiles (linear interpolation), the mask cut
+//                        and the OCT threshold (float64, one thread)
+//   project_kernel       per A-scan (one warp): mean of the OCTA voxels whose
+//                        filtered value is below the cut and whose OCT value
+//                        is above the threshold
+//   bscan_median_kernel  median of each B-scan's en-face values (bitonic sort
+//                        in shared memory) subtracted from them
+//   replace_kernel       invalid B-scans take the nearest valid one
+//
+// Volumes are float32 [h][w][d], depth contiguous.  B-scans of an X-fast
+// scan (fast_axis 0) are the rows j, of a Y-fast scan the columns i.
+#include <cmath>
+#include <new>
+
+#include "common.cuh"
+
+namespace octmc {
+namespace {
+
+constexpr int kT = 256;
+constexpr int kRadixBins = 2048;
+constexpr int kTargets = 4;  // order statistics: floor/ceil positions of two percentiles
+
+struct Select {
+  // per target: rank (0-based) among the selected voxels, key prefix found so
+  // far, and the value once known
+  long long rank[kTargets];
+  unsigned prefix[kTargets];
+  float value[kTargets];
+  double pos[2];      // q (n - 1) of the two percentiles
+  double p[2];        // the percentiles
+  double cut;         // p_lo + thresh (p_hi - p_lo)
+  double t_oct;       // OCT threshold
+  float cut_f;        // smallest float >= cut: x < cut  <=>  x < cut_f
+  float toct_f;       // largest float <= t_oct: x > t_oct <=> x > toct_f
+};
+
+__device__ __forceinline__ int64_t ascan_of(int w, int fast_axis, int b, int f) {
+  return fast_axis == 0 ? (int64_t)b * w + f : (int64_t)f * w + b;
+}
+
+// ---------------------------------------------------------------- sums
+// Block b sums the voxels of B-scan b (nf columns of d samples).
+__global__ void __launch_bounds__(kT) bscan_sum_kernel(const float* __restrict__ vol, int w, int h, int d,
+                                                       int fast_axis, double* __restrict__ sums) {
+  const int b = blockIdx.x;
+  const int nf = fast_axis == 0 ? w : h;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double acc = 0.0;  // every sample widened and added in float64 (no float rounding)
+  for (int f = warp; f < nf; f += kT / 32) {
+    const float* col = vol + ascan_of(w, fast_axis, b, f) * d;
+    for (int k = lane; k < d; k += 32) acc += widen_exact(col[k]);
+  }
+  acc = warp_sum(acc);
+  __shared__ double sm[kT / 32];
+  if (lane == 0) sm[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < kT / 32; i++) t += sm[i];
+    sums[b] = t;
+  }
+}
+
+// One block: means, mu, sigma, saturation test, validity.
+__global__ void __launch_bounds__(1024) validity_kernel(const double* __restrict__ sums, int nb, double per,
+                                                        float* __restrict__ v, double* __restrict__ means) {
+  __shared__ double sm[32];
+  __shared__ double s_mu, s_sig;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double a = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) a += sums[b] / per;
+  a = warp_sum(a);
+  if (lane == 0) sm[warp] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < nw; i++) t += sm[i];
+    s_mu = t / nb;
+  }
+  __syncthreads();
+  const double mu = s_mu;
+  double q = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    const double m = sums[b] / per;
+    q += (m - mu) * (m - mu);
+  }
+  q = warp_sum(q);
+  __syncthreads();
+  if (lane == 0) sm[warp] = q;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < nw; i++) t += sm[i];
+    s_sig = sqrt(t / nb);
+  }
+  __syncthreads();
+  const double lim = mu + 3.0 * s_sig;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    bool ok = true;
+    for (int o = -2; o <= 2; o++) {
+      const int c = b + o;
+      if (c >= 0 && c < nb && sums[c] / per > lim) ok = false;
+    }
+    v[b] = ok ? 1.0f : 0.0f;
+    if (means) means[b] = sums[b] / per;
+  }
+}
+
+// ---------------------------------------------------------------- filters
+__device__ __forceinline__ int clampn(int i, int n) { return i < 0 ? 0 : (i >= n ? n - 1 : i); }
+
+// a[lo] <- min of a[lo..14], a[14] <- max of a[lo..14] (others permuted).
+template <int LO>
+__device__ __forceinline__ void minmax_pass(float (&a)[15]) {
+  float mn = fminf(a[LO], a[14]), mx = fmaxf(a[LO], a[14]);
+  a[LO] = mn;
+  a[14] = mx;
+#pragma unroll
+  for (int i = LO + 1; i < 14; i++) {
+    mn = fminf(a[LO], a[i]);
+    mx = fmaxf(a[LO], a[i]);
+    a[LO] = mn;
+    a[i] = mx;
+    mn = fminf(a[i], a[14]);
+    mx = fmaxf(a[i], a[14]);
+    a[i] = mn;
+    a[14] = mx;
+  }
+}
+
+template <int LO>
+__device__ __forceinline__ void forget_steps(float (&a)[15], const float (&rest)[12]) {
+  if constexpr (LO < 12) {
+    minmax_pass<LO>(a);
+    a[14] = rest[LO];  // the maximum is forgotten, the next sample takes its place
+    forget_steps<LO + 1>(a, rest);
+  }
+}
+
+__global__ void __launch_bounds__(kT) median3_kernel(const float* __restrict__ in, int w, int h, int d,
+                                                     float* __restrict__ out) {
+  const int64_t n = (int64_t)w * h * d;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e % d);
+    const int64_t p = e / d;
+    const int i = (int)(p % w), j = (int)(p / w);
+    float v[27];
+    int c = 0;
+#pragma unroll
+    for (int dj = -1; dj <= 1; dj++)
+#pragma unroll
+      for (int di = -1; di <= 1; di++) {
+        const float* col = in + ((int64_t)clampn(j + dj, h) * w + clampn(i + di, w)) * d;
+#pragma unroll
+        for (int dk = -1; dk <= 1; dk++) v[c++] = __ldg(col + clampn(k + dk, d));
+      }
+    float a[15], rest[12];
+#pragma unroll
+    for (int t = 0; t < 15; t++) a[t] = v[t];
+#pragma unroll
+    for (int t = 0; t < 12; t++) rest[t] = v[15 + t];
+    // 12 steps: each drops the minimum (window start moves) and the maximum
+    // (replaced by the next sample); 3 candidates remain, the median is
+    // their middle value
+    forget_steps<0>(a, rest);
+    const float x = a[12], y = a[13], z = a[14];
+    out[e] = fmaxf(fminf(x, y), fminf(fmaxf(x, y), z));
+  }
+}
+
+__global__ void __launch_bounds__(kT) rank15_kernel(const float* __restrict__ in, int w, int h, int d, int axis,
+                                                    float* __restrict__ out) {
+  const int64_t n = (int64_t)w * h * d;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e % d);
+    const int64_t p = e / d;
+    const int i = (int)(p % w), j = (int)(p / w);
+    float a1 = INFINITY, a2 = INFINITY, a3 = INFINITY;
+#pragma unroll
+    for (int o = -7; o <= 7; o++) {
+      const int ii = axis == 0 ? clampn(i + o, w) : i;
+      const int jj = axis == 1 ? clampn(j + o, h) : j;
+      const float x = __ldg(in + ((int64_t)jj * w + ii) * d + k);
+      const float t = fmaxf(a1, x);
+      a1 = fminf(a1, x);
+      const float u = fmaxf(a2, t);
+      a2 = fminf(a2, t);
+      a3 = fminf(a3, u);
+    }
+    out[e] = a3;
+  }
+}
+
+// ---------------------------------------------------------------- selection
+__device__ __forceinline__ unsigned order_key(float x) {
+  const unsigned u = __float_as_uint(x);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key_value(unsigned k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// digit pass `pass` (0: bits 31..21, 1: 20..10, 2: 9..0)
+__device__ __forceinline__ int digit_shift(int pass) { return pass == 0 ? 21 : (pass == 1 ? 10 : 0); }
+__device__ __forceinline__ unsigned digit_mask(int pass) { return pass == 2 ? 0x3ffu : 0x7ffu; }
+
+// Histogram of the current digit of the selected voxels whose higher digits
+// equal each target's prefix.  hist [kTargets][kRadixBins].
+__global__ void __launch_bounds__(kT) radix_hist_kernel(const float* __restrict__ vol, int w, int h, int d,
+                                                        int fast_axis, const float* __restrict__ v, int any_valid,
+                                                        const Select* __restrict__ sel, int pass,
+                                                        unsigned* __restrict__ hist) {
+  __shared__ unsigned sh[kTargets][kRadixBins];
+  for (int t = threadIdx.x; t < kTargets * kRadixBins; t += kT) (&sh[0][0])[t] = 0u;
+  __syncthreads();
+  const int sft = digit_shift(pass);
+  const unsigned msk = digit_mask(pass);
+  unsigned pre[kTargets];
+#pragma unroll
+  for (int t = 0; t < kTargets; t++) pre[t] = sel->prefix[t];
+  const int hs = sft + (pass == 0 ? 11 : (pass == 1 ? 11 : 10));  // bits above the digit: >= hs
+  const int64_t n = (int64_t)w * h * d;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = e / d;
+    const int b = fast_axis == 0 ? (int)(p / w) : (int)(p % w);
+    if (any_valid && v[b] == 0.0f) continue;
+    const unsigned key = order_key(vol[e]);
+    const unsigned dig = (key >> sft) & msk;
+    const unsigned hi = hs >= 32 ? 0u : (key >> hs);
+#pragma unroll
+    for (int t = 0; t < kTargets; t++)
+      if (hi == pre[t]) atomicAdd(&sh[t][dig], 1u);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < kTargets * kRadixBins; t += kT) {
+    const unsigned c = (&sh[0][0])[t];
+    if (c) atomicAdd(hist + t, c);
+  }
+}
+
+// One block: for each target, the bin holding its rank; prefix and rank are
+// narrowed to that bin.  After the last pass the key is complete.
+__global__ void radix_pick_kernel(Select* sel, unsigned* hist, int pass) {
+  const int t = threadIdx.x;
+  if (t < kTargets) {
+    const unsigned nbins = digit_mask(pass) + 1u;
+    const unsigned* hb = hist + t * kRadixBins;
+    long long r = sel->rank[t];
+    unsigned bin = 0;
+    for (; bin < nbins; bin++) {
+      if (r < (long long)hb[bin]) break;
+      r -= hb[bin];
+    }
+    if (bin >= nbins) bin = nbins - 1;  // not reached for a valid rank
+    const int width = pass == 2 ? 10 : 11;
+    sel->prefix[t] = (sel->prefix[t] << width) | bin;
+    sel->rank[t] = r;
+    if (pass == 2) sel->value[t] = key_value(sel->prefix[t]);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kTargets * kRadixBins; i += blockDim.x) hist[i] = 0u;
+}
+
+__global__ void finish_kernel(Select* sel, const double* __restrict__ oct_sums, const float* __restrict__ v,
+                              int nb, int any_valid, double per_bscan, double thresh, double t_oct_in) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int q = 0; q < 2; q++) {
+    const double pos = sel->pos[q];
+    const double lo = floor(pos);
+    const double a = sel->value[2 * q], b = sel->value[2 * q + 1];
+    sel->p[q] = a + (pos - lo) * (b - a);
+  }
+  sel->cut = sel->p[0] + thresh * (sel->p[1] - sel->p[0]);
+  double t = t_oct_in;
+  if (isnan(t)) {
+    double s = 0.0, cnt = 0.0;
+    for (int b = 0; b < nb; b++)
+      if (!any_valid || v[b] != 0.0f) {
+        s += oct_sums[b];
+        cnt += per_bscan;
+      }
+    t = s / cnt;
+  }
+  sel->t_oct = t;
+  // float bounds that reproduce the double comparisons exactly
+  float c = (float)sel->cut;  // round to nearest
+  if ((double)c < sel->cut) c = nextafterf(c, INFINITY);
+  else if ((double)nextafterf(c, -INFINITY) >= sel->cut) c = nextafterf(c, -INFINITY);
+  sel->cut_f = c;
+  float o = (float)t;
+  if ((double)o > t) o = nextafterf(o, -INFINITY);
+  sel->toct_f = o;
+}
+
+// ---------------------------------------------------------------- projection
+// One warp per A-scan.
+__global__ void __launch_bounds__(kT) project_kernel(const float* __restrict__ A, const float* __restrict__ S,
+                                                     const float* __restrict__ F, int64_t nasc, int d,
+                                                     const Select* __restrict__ sel, float* __restrict__ E,
+                                                     unsigned long long* __restrict__ kept) {
+  const int lane = threadIdx.x & 31;
+  const float cut = sel->cut_f, to = sel->toct_f;
+  for (int64_t p = (int64_t)blockIdx.x * (kT / 32) + (threadIdx.x >> 5); p < nasc;
+       p += (int64_t)gridDim.x * (kT / 32)) {  // warp-uniform
+    float s = 0.f;
+    int c = 0;
+    for (int k = lane; k < d; k += 32) {
+      const int64_t e = p * d + k;
+      if (F[e] < cut && S[e] > to) {
+        s += A[e];
+        c++;
+      }
+    }
+    s = warp_sum(s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) {
+      E[p] = c ? s / (float)c : 0.0f;
+      if (c) atomicAdd(kept, (unsigned long long)c);
+    }
+  }
+}
+
+// One block per B-scan: bitonic sort of its en-face values in shared memory,
+// median, subtraction.  nf <= kMaxFast.
+constexpr int kMaxFast = 4096;
+__global__ void __launch_bounds__(1024) bscan_median_kernel(float* __restrict__ E, int w, int h, int fast_axis) {
+  __shared__ float s[kMaxFast];
+  const int b = blockIdx.x;
+  const int nf = fast_axis == 0 ? w : h;
+  int np = 1;
+  while (np < nf) np <<= 1;
+  for (int f = threadIdx.x; f < np; f += blockDim.x) s[f] = f < nf ? E[ascan_of(w, fast_axis, b, f)] : INFINITY;
+  __syncthreads();
+  for (int size = 2; size <= np; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        const int jx = i ^ stride;
+        if (jx > i) {
+          const bool up = (i & size) == 0;
+          const float x = s[i], y = s[jx];
+          if ((x > y) == up) {
+            s[i] = y;
+            s[jx] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  const double med = (nf & 1) ? (double)s[nf / 2] : 0.5 * ((double)s[nf / 2 - 1] + (double)s[nf / 2]);
+  __syncthreads();
+  for (int f = threadIdx.x; f < nf; f += blockDim.x) {
+    float* e = E + ascan_of(w, fast_axis, b, f);
+    *e = (float)((double)*e - med);
+  }
+}
+
+// Block per B-scan: an invalid B-scan copies the nearest valid one (lower
+// index on a tie) from src (the subtracted image before replacement).
+__global__ void replace_kernel(const float* __restrict__ src, float* __restrict__ E, int w, int h, int fast_axis,
+                               const float* __restrict__ v) {
+  const int b = blockIdx.x;
+  const int nb = fast_axis == 0 ? h : w, nf = fast_axis == 0 ? w : h;
+  if (v[b] != 0.0f) return;
+  int best = -1;
+  for (int dist = 1; dist < nb && best < 0; dist++) {
+    if (b - dist >= 0 && v[b - dist] != 0.0f) best = b - dist;
+    else if (b + dist < nb && v[b + dist] != 0.0f) best = b + dist;
+  }
+  if (best < 0) return;
+  for (int f = threadIdx.x; f < nf; f += blockDim.x) E[ascan_of(w, fast_axis, b, f)] = src[ascan_of(w, fast_axis, best, f)];
+}
+
+inline unsigned grid_for(int64_t n, int per = kT) {
+  int64_t b = (n + per - 1) / per;
+  if (b < 1) b = 1;
+  if (b > 152 * 64) b = 152 * 64;
+  return (unsigned)b;
+}
+
+struct CudaErr {
+  cudaError_t e;
+};
+inline void ck(cudaError_t e) {
+  if (e != cudaSuccess) throw CudaErr{e};
+}
+
+}  // namespace
+}  // namespace octmc
+
+using namespace octmc;
+
+extern "C" int octmc_saccade_validity(const float* octa, int w, int h, int d, int fast_axis, float* v,
+                                      double* means, void* stream) {
+  if (!octa || !v || w < 1 || h < 1 || d < 1 || (fast_axis != 0 && fast_axis != 1)) return OCTMC_ERR_INVALID_ARG;
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int nb = fast_axis == 0 ? h : w, nf = fast_axis == 0 ? w : h;
+  double* sums = nullptr;
+  try {
+    ck(cudaMallocAsync(&sums, sizeof(double) * nb, st));
+    bscan_sum_kernel<<<nb, kT, 0, st>>>(octa, w, h, d, fast_axis, sums);
+    ck(cudaGetLastError());
+    validity_kernel<<<1, 1024, 0, st>>>(sums, nb, (double)nf * d, v, means);
+    ck(cudaGetLastError());
+    ck(cudaFreeAsync(sums, st));
+    ck(cudaStreamSynchronize(st));
+  } catch (const CudaErr&) {
+    cudaGetLastError();
+    return OCTMC_ERR_CUDA;
+  }
+  return OCTMC_OK;
+}
+
+extern "C" int octmc_enface(const float* octa, const float* oct, int w, int h, int d, int fast_axis, const float* v,
+                            double q_lo, double q_hi, double thresh, double t_oct, float* enface, float* filtered,
+                            double* info, void* stream) {
+  if (!octa || !oct || !v || !enface || w < 1 || h < 1 || d < 1 || (fast_axis != 0 && fast_axis != 1))
+    return OCTMC_ERR_INVALID_ARG;
+  if (!(q_lo >= 0.0 && q_lo <= 1.0 && q_hi >= 0.0 && q_hi <= 1.0) || !std::isfinite(thresh))
+    return OCTMC_ERR_INVALID_ARG;
+  const int nb = fast_axis == 0 ? h : w, nf = fast_axis == 0 ? w : h;
+  if (nf > kMaxFast) return OCTMC_ERR_UNSUPPORTED;
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int64_t nvox = (int64_t)w * h * d, nasc = (int64_t)w * h;
+  // validity is needed on the host for the selected-voxel count
+  float* vh = nullptr;
+  float *m3 = nullptr, *r1 = nullptr, *r2 = nullptr, *esrc = nullptr;
+  double* osum = nullptr;
+  Select* sel = nullptr;
+  unsigned* hist = nullptr;
+  unsigned long long* kept = nullptr;
+  int rc = OCTMC_OK;
+  try {
+    vh = new float[nb];
+    ck(cudaMemcpyAsync(vh, v, sizeof(float) * nb, cudaMemcpyDeviceToHost, st));
+    ck(cudaStreamSynchronize(st));
+    int nvalid = 0;
+    for (int b = 0; b < nb; b++) nvalid += vh[b] != 0.0f;
+    const int any = nvalid > 0;
+    const long long nsel = (long long)(any ? nvalid : nb) * nf * d;
+    Select s0{};
+    const double qs[2] = {q_lo, q_hi};
+    for (int q = 0; q < 2; q++) {
+      s0.pos[q] = qs[q] * (double)(nsel - 1);
+      const long long lo = (long long)std::floor(s0.pos[q]);
+      s0.rank[2 * q] = lo;
+      s0.rank[2 * q + 1] = lo + 1 < nsel ? lo + 1 : lo;
+    }
+    ck(cudaMallocAsync(&m3, sizeof(float) * nvox, st));
+    ck(cudaMallocAsync(&r1, sizeof(float) * nvox, st));
+    r2 = filtered;
+    if (!r2) ck(cudaMallocAsync(&r2, sizeof(float) * nvox, st));
+    ck(cudaMallocAsync(&osum, sizeof(double) * nb, st));
+    ck(cudaMallocAsync(&sel, sizeof(Select), st));
+    ck(cudaMallocAsync(&hist, sizeof(unsigned) * kTargets * kRadixBins, st));
+    ck(cudaMallocAsync(&kept, sizeof(unsigned long long), st));
+    ck(cudaMallocAsync(&esrc, sizeof(float) * nasc, st));
+    ck(cudaMemcpyAsync(sel, &s0, sizeof(Select), cudaMemcpyHostToDevice, st));
+    ck(cudaMemsetAsync(hist, 0, sizeof(unsigned) * kTargets * kRadixBins, st));
+    ck(cudaMemsetAsync(kept, 0, sizeof(unsigned long long), st));
+    // filters
+    median3_kernel<<<grid_for(nvox), kT, 0, st>>>(octa, w, h, d, m3);
+    ck(cudaGetLastError());
+    rank15_kernel<<<grid_for(nvox), kT, 0, st>>>(m3, w, h, d, fast_axis, r1);
+    ck(cudaGetLastError());
+    rank15_kernel<<<grid_for(nvox), kT, 0, st>>>(r1, w, h, d, 1 - fast_axis, r2);
+    ck(cudaGetLastError());
+    // percentiles of the filtered voxels of the valid B-scans
+    for (int pass = 0; pass < 3; pass++) {
+      radix_hist_kernel<<<grid_for(nvox), kT, 0, st>>>(r2, w, h, d, fast_axis, v, any, sel, pass, hist);
+      ck(cudaGetLastError());
+      radix_pick_kernel<<<1, 256, 0, st>>>(sel, hist, pass);
+      ck(cudaGetLastError());
+    }
+    // OCT threshold from the per-B-scan OCT sums, cut, projection
+    if (std::isnan(t_oct)) {
+      bscan_sum_kernel<<<nb, kT, 0, st>>>(oct, w, h, d, fast_axis, osum);
+      ck(cudaGetLastError());
+    }
+    finish_kernel<<<1, 32, 0, st>>>(sel, osum, v, nb, any, (double)nf * d, thresh, t_oct);
+    ck(cudaGetLastError());
+    project_kernel<<<grid_for(nasc, kT / 32), kT, 0, st>>>(octa, oct, r2, nasc, d, sel, enface, kept);
+    ck(cudaGetLastError());
+    bscan_median_kernel<<<nb, 1024, 0, st>>>(enface, w, h, fast_axis);
+    ck(cudaGetLastError());
+    if (any && nvalid < nb) {
+      ck(cudaMemcpyAsync(esrc, enface, sizeof(float) * nasc, cudaMemcpyDeviceToDevice, st));
+      replace_kernel<<<nb, 256, 0, st>>>(esrc, enface, w, h, fast_axis, v);
+      ck(cudaGetLastError());
+    }
+    if (info) {
+      Select s1;
+      unsigned long long kh = 0;
+      ck(cudaMemcpyAsync(&s1, sel, sizeof(Select), cudaMemcpyDeviceToHost, st));
+      ck(cudaMemcpyAsync(&kh, kept, sizeof(kh), cudaMemcpyDeviceToHost, st));
+      ck(cudaStreamSynchronize(st));
+      info[0] = s1.p[0];
+      info[1] = s1.p[1];
+      info[2] = s1.t_oct;
+      info[3] = (double)kh;
+    }
+  } catch (const CudaErr&) {
+    cudaGetLastError();
+    rc = OCTMC_ERR_CUDA;
+  } catch (const std::bad_alloc&) {
+    rc = OCTMC_ERR_OOM;
+  }
+  if (m3) cudaFreeAsync(m3, st);
+  if (r1) cudaFreeAsync(r1, st);
+  if (r2 && r2 != filtered) cudaFreeAsync(r2, st);
+  if (osum) cudaFreeAsync(osum, st);
+  if (sel) cudaFreeAsync(sel, st);
+  if (hist) cudaFreeAsync(hist, st);
+  if (kept) cudaFreeAsync(kept, st);
+  if (esrc) cudaFreeAsync(esrc, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess && rc == OCTMC_OK) rc = OCTMC_ERR_CUDA;
+  delete[] vh;
+  return rc;
+}
