@@ -55,6 +55,40 @@ def merge_bytes(w, h, d, s=4):
     return n * (2 * d * s + d * 4 + 2 * 48 + 3 * 16 + 2 * 8 + 8 + 4)
 
 
+def enface_bytes(w, h, d):
+    """Algorithmic bytes of the validity + en-face projection of one scan:
+    validity (OCTA read once), median (read + write), two rank filters (read
+    + write each), three radix passes (read), the OCT sums (read), the
+    projection (OCTA, OCT and filtered volumes read), the image (write)."""
+    v = w * h * d * 4
+    return v * (1 + 2 + 4 + 3 + 1 + 3) + w * h * 4
+
+
+def time_enface(octmc, w, h, d, e0, e1, stream, barrier, reps=5):
+    from octsynth import make_octa_scan
+    import torch
+    sc = make_octa_scan(w, h, d, fast_axis=0, n_slabs=3, n_saturated=3, seed=2002)
+    A = torch.from_numpy(sc["A"]).cuda()
+    S = torch.from_numpy(sc["S"]).cuda()
+    E = torch.empty((h, w), dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        v, _ = octmc.saccade_validity(A, 0)
+        octmc.enface(A, S, 0, v, out=E)
+    barrier()
+    e0.record(stream)
+    for _ in range(reps):
+        v, _ = octmc.saccade_validity(A, 0)
+        _, info = octmc.enface(A, S, 0, v, out=E)
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1) / reps
+    B = enface_bytes(w, h, d)
+    return {"ms_per_scan": ms, "bytes": B, "gbs": B / ms / 1e6, "invalid_bscans": int((v == 0).sum()),
+            "kept_voxels": info["kept"],
+            "workload": "one synthetic OCTA + OCT scan %dx%d A-scans x %d, 3 saturated B-scans" % (w, h, d),
+            "note": "saccade validity + en-face projection, host sync per call"}
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -64,6 +98,7 @@ def parse_args():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-octa", action="store_true", help="skip the en-face projection timing")
     ap.add_argument("--serve", action="store_true",
                     help="serving workload instead: Poisson arrivals of mixed-size BF16 pairs")
     ap.add_argument("--serve-requests", type=int, default=200)
@@ -327,6 +362,11 @@ def run_ours(args):
     merge = {"ms": merge_ms, "bytes": mb, "gbs": mb / merge_ms / 1e6, "outputs": list(mo),
              "note": "weights (density splat + gather) and resample-merge kernels, one host sync per call"}
 
+    # ---- angiography preprocessing of one scan of the pair's size (Sec. 2.2, 2.3)
+    enf = None
+    if not args.no_octa:
+        enf = time_enface(octmc, w, h, d, e0, e1, stream, barrier)
+
     # max over ranks
     t = torch.tensor([ms, ms_e2e], dtype=torch.float64, device="cuda")
     if dist is not None:
@@ -340,6 +380,8 @@ def run_ours(args):
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     alu_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
     merge["hbm_frac"] = merge["gbs"] / hbm_peak
+    if enf is not None:
+        enf["hbm_frac"] = enf["gbs"] / hbm_peak
     kavg = kern_ms / max(kern_n, 1) / 1e3
     F = flops_per_eval(w, h, d)
     B = bytes_per_eval(w, h, d)
@@ -365,6 +407,7 @@ def run_ours(args):
         "clocks": clk,
         "solve": solve,
         "merge": merge,
+        "enface": enf,
     }
     if not args.no_cpu and ws == 1:
         line["cpu_baseline"] = cpu_baseline(pair, cfg)

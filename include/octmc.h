@@ -199,7 +199,7 @@ int octmc_saccade_validity(const float *octa_dev, int w, int h, int d, int fast_
  * receives the rank-filtered volume; info_host (may be NULL) receives
  * [q_lo quantile, q_hi quantile, t_oct, voxels in both masks].  The paper
  * uses q_lo = 0.05, q_hi = 0.95, thresh = 0.1.  Inputs must be finite.
- * Errors: INVALID_ARG, UNSUPPORTED (more than 4096 A-scans per B-scan), OOM,
+ * Errors: INVALID_ARG, UNSUPPORTED (more than 4096 A-scans per B-scan, h > 65535), OOM,
  * CUDA. */
 int octmc_enface(const float *octa_dev, const float *oct_dev, int w, int h, int d, int fast_axis,
                  const float *v_dev, double q_lo, double q_hi, double thresh, double t_oct, float *enface_dev,

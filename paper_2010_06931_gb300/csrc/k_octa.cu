@@ -27,6 +27,7 @@
 //
 // Volumes are float32 [h][w][d], depth contiguous.  B-scans of an X-fast
 // scan (fast_axis 0) are the rows j, of a Y-fast scan the columns i.
+#include <algorithm>
 #include <cmath>
 #include <new>
 
@@ -59,23 +60,31 @@ __device__ __forceinline__ int64_t ascan_of(int w, int fast_axis, int b, int f) 
 
 // ---------------------------------------------------------------- sums
 // Block b sums the voxels of B-scan b (nf columns of d samples).
-__global__ void __launch_bounds__(kT) bscan_sum_kernel(const float* __restrict__ vol, int w, int h, int d,
-                                                       int fast_axis, double* __restrict__ sums) {
+constexpr int kSumThreads = 1024;
+__global__ void __launch_bounds__(kSumThreads) bscan_sum_kernel(const float* __restrict__ vol, int w, int h, int d,
+                                                                int fast_axis, double* __restrict__ sums) {
   const int b = blockIdx.x;
   const int nf = fast_axis == 0 ? w : h;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double acc = 0.0;  // every sample widened and added in float64 (no float rounding)
-  for (int f = warp; f < nf; f += kT / 32) {
+  // every sample widened and added in float64 (no float rounding); two
+  // independent chains per lane for the float64 latency
+  double acc0 = 0.0, acc1 = 0.0;
+  for (int f = warp; f < nf; f += kSumThreads / 32) {
     const float* col = vol + ascan_of(w, fast_axis, b, f) * d;
-    for (int k = lane; k < d; k += 32) acc += widen_exact(col[k]);
+    int k = lane;
+    for (; k + 32 < d; k += 64) {
+      acc0 += widen_exact(col[k]);
+      acc1 += widen_exact(col[k + 32]);
+    }
+    if (k < d) acc0 += widen_exact(col[k]);
   }
-  acc = warp_sum(acc);
-  __shared__ double sm[kT / 32];
+  double acc = warp_sum(acc0 + acc1);
+  __shared__ double sm[kSumThreads / 32];
   if (lane == 0) sm[warp] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int i = 0; i < kT / 32; i++) t += sm[i];
+    for (int i = 0; i < kSumThreads / 32; i++) t += sm[i];
     sums[b] = t;
   }
 }
@@ -156,58 +165,60 @@ __device__ __forceinline__ void forget_steps(float (&a)[15], const float (&rest)
   }
 }
 
-__global__ void __launch_bounds__(kT) median3_kernel(const float* __restrict__ in, int w, int h, int d,
-                                                     float* __restrict__ out) {
-  const int64_t n = (int64_t)w * h * d;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    const int k = (int)(e % d);
-    const int64_t p = e / d;
-    const int i = (int)(p % w), j = (int)(p / w);
-    float v[27];
-    int c = 0;
+// Stencil launch geometry: block (32 depths, 8 columns i), grid (depth
+// chunks, column chunks, rows j): no index division, warps read 128 coalesced
+// bytes along depth, and blocks run in volume order so the rows a wave reads
+// stay in L2.
+constexpr int kSx = 32, kSy = 8;
+
+__global__ void __launch_bounds__(kSx * kSy) median3_kernel(const float* __restrict__ in, int w, int h, int d,
+                                                            float* __restrict__ out) {
+  const int k = blockIdx.x * kSx + threadIdx.x;
+  const int i = blockIdx.y * kSy + threadIdx.y;
+  const int j = blockIdx.z;
+  if (k >= d || i >= w) return;
+  float v[27];
+  int c = 0;
 #pragma unroll
-    for (int dj = -1; dj <= 1; dj++)
+  for (int dj = -1; dj <= 1; dj++)
 #pragma unroll
-      for (int di = -1; di <= 1; di++) {
-        const float* col = in + ((int64_t)clampn(j + dj, h) * w + clampn(i + di, w)) * d;
+    for (int di = -1; di <= 1; di++) {
+      const float* col = in + ((int64_t)clampn(j + dj, h) * w + clampn(i + di, w)) * d;
 #pragma unroll
-        for (int dk = -1; dk <= 1; dk++) v[c++] = __ldg(col + clampn(k + dk, d));
-      }
-    float a[15], rest[12];
+      for (int dk = -1; dk <= 1; dk++) v[c++] = __ldg(col + clampn(k + dk, d));
+    }
+  float a[15], rest[12];
 #pragma unroll
-    for (int t = 0; t < 15; t++) a[t] = v[t];
+  for (int t = 0; t < 15; t++) a[t] = v[t];
 #pragma unroll
-    for (int t = 0; t < 12; t++) rest[t] = v[15 + t];
-    // 12 steps: each drops the minimum (window start moves) and the maximum
-    // (replaced by the next sample); 3 candidates remain, the median is
-    // their middle value
-    forget_steps<0>(a, rest);
-    const float x = a[12], y = a[13], z = a[14];
-    out[e] = fmaxf(fminf(x, y), fminf(fmaxf(x, y), z));
-  }
+  for (int t = 0; t < 12; t++) rest[t] = v[15 + t];
+  // 12 steps: each drops the minimum (window start moves) and the maximum
+  // (replaced by the next sample); 3 candidates remain, the median is their
+  // middle value
+  forget_steps<0>(a, rest);
+  const float x = a[12], y = a[13], z = a[14];
+  out[((int64_t)j * w + i) * d + k] = fmaxf(fminf(x, y), fminf(fmaxf(x, y), z));
 }
 
-__global__ void __launch_bounds__(kT) rank15_kernel(const float* __restrict__ in, int w, int h, int d, int axis,
-                                                    float* __restrict__ out) {
-  const int64_t n = (int64_t)w * h * d;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    const int k = (int)(e % d);
-    const int64_t p = e / d;
-    const int i = (int)(p % w), j = (int)(p / w);
-    float a1 = INFINITY, a2 = INFINITY, a3 = INFINITY;
+__global__ void __launch_bounds__(kSx * kSy) rank15_kernel(const float* __restrict__ in, int w, int h, int d,
+                                                           int axis, float* __restrict__ out) {
+  const int k = blockIdx.x * kSx + threadIdx.x;
+  const int i = blockIdx.y * kSy + threadIdx.y;
+  const int j = blockIdx.z;
+  if (k >= d || i >= w) return;
+  float a1 = INFINITY, a2 = INFINITY, a3 = INFINITY;
 #pragma unroll
-    for (int o = -7; o <= 7; o++) {
-      const int ii = axis == 0 ? clampn(i + o, w) : i;
-      const int jj = axis == 1 ? clampn(j + o, h) : j;
-      const float x = __ldg(in + ((int64_t)jj * w + ii) * d + k);
-      const float t = fmaxf(a1, x);
-      a1 = fminf(a1, x);
-      const float u = fmaxf(a2, t);
-      a2 = fminf(a2, t);
-      a3 = fminf(a3, u);
-    }
-    out[e] = a3;
+  for (int o = -7; o <= 7; o++) {
+    const int ii = axis == 0 ? clampn(i + o, w) : i;
+    const int jj = axis == 1 ? clampn(j + o, h) : j;
+    const float x = __ldg(in + ((int64_t)jj * w + ii) * d + k);
+    const float t = fmaxf(a1, x);
+    a1 = fminf(a1, x);
+    const float u = fmaxf(a2, t);
+    a2 = fminf(a2, t);
+    a3 = fminf(a3, u);
   }
+  out[((int64_t)j * w + i) * d + k] = a3;
 }
 
 // ---------------------------------------------------------------- selection
@@ -224,7 +235,13 @@ __device__ __forceinline__ int digit_shift(int pass) { return pass == 0 ? 21 : (
 __device__ __forceinline__ unsigned digit_mask(int pass) { return pass == 2 ? 0x3ffu : 0x7ffu; }
 
 // Histogram of the current digit of the selected voxels whose higher digits
-// equal each target's prefix.  hist [kTargets][kRadixBins].
+// equal each target's prefix.  hist [kTargets][kRadixBins].  Targets with
+// the same prefix share one count (slot[t] = first target with t's
+// prefix).  Each thread takes runs of kRun consecutive voxels and counts
+// equal consecutive digits in registers before one shared atomic per run of
+// equal digits: the filtered volume is smooth along depth, so the few hot
+// bins of the leading digit (sign and exponent) are not hammered.
+constexpr int kRun = 16;
 __global__ void __launch_bounds__(kT) radix_hist_kernel(const float* __restrict__ vol, int w, int h, int d,
                                                         int fast_axis, const float* __restrict__ v, int any_valid,
                                                         const Select* __restrict__ sel, int pass,
@@ -235,49 +252,101 @@ __global__ void __launch_bounds__(kT) radix_hist_kernel(const float* __restrict_
   const int sft = digit_shift(pass);
   const unsigned msk = digit_mask(pass);
   unsigned pre[kTargets];
+  int slot[kTargets];
 #pragma unroll
-  for (int t = 0; t < kTargets; t++) pre[t] = sel->prefix[t];
-  const int hs = sft + (pass == 0 ? 11 : (pass == 1 ? 11 : 10));  // bits above the digit: >= hs
+  for (int t = 0; t < kTargets; t++) {
+    pre[t] = sel->prefix[t];
+    slot[t] = t;
+    for (int u = t - 1; u >= 0; u--)
+      if (pre[u] == pre[t]) slot[t] = u;
+  }
+  const int hs = sft + (pass == 2 ? 10 : 11);  // the bits above the digit start at hs
   const int64_t n = (int64_t)w * h * d;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p = e / d;
-    const int b = fast_axis == 0 ? (int)(p / w) : (int)(p % w);
-    if (any_valid && v[b] == 0.0f) continue;
-    const unsigned key = order_key(vol[e]);
-    const unsigned dig = (key >> sft) & msk;
-    const unsigned hi = hs >= 32 ? 0u : (key >> hs);
+  const int64_t nrun = (n + kRun - 1) / kRun;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrun; r += (int64_t)gridDim.x * blockDim.x) {
+    int64_t e = r * kRun;
+    int64_t p = e / d;
+    int k = (int)(e - p * d);
+    unsigned cur[kTargets], cnt[kTargets];
+#pragma unroll
+    for (int t = 0; t < kTargets; t++) {
+      cur[t] = 0u;
+      cnt[t] = 0u;
+    }
+    for (int q = 0; q < kRun && e < n; q++, e++) {
+      const int b = fast_axis == 0 ? (int)(p / w) : (int)(p % w);
+      if (!(any_valid && v[b] == 0.0f)) {
+        const unsigned key = order_key(vol[e]);
+        const unsigned dig = (key >> sft) & msk;
+        const unsigned hi = hs >= 32 ? 0u : (key >> hs);
+#pragma unroll
+        for (int t = 0; t < kTargets; t++) {
+          if (slot[t] != t || hi != pre[t]) continue;
+          if (cnt[t] && dig != cur[t]) {
+            atomicAdd(&sh[t][cur[t]], cnt[t]);
+            cnt[t] = 0u;
+          }
+          cur[t] = dig;
+          cnt[t]++;
+        }
+      }
+      if (++k == d) {
+        k = 0;
+        p++;
+      }
+    }
 #pragma unroll
     for (int t = 0; t < kTargets; t++)
-      if (hi == pre[t]) atomicAdd(&sh[t][dig], 1u);
+      if (cnt[t]) atomicAdd(&sh[t][cur[t]], cnt[t]);
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < kTargets * kRadixBins; t += kT) {
-    const unsigned c = (&sh[0][0])[t];
-    if (c) atomicAdd(hist + t, c);
+  for (int i = threadIdx.x; i < kTargets * kRadixBins; i += kT) {
+    const int t = i / kRadixBins, bin = i % kRadixBins;
+    const int st = t == 0 ? slot[0] : (t == 1 ? slot[1] : (t == 2 ? slot[2] : slot[3]));
+    const unsigned c = sh[st][bin];
+    if (c) atomicAdd(hist + i, c);
   }
 }
 
-// One block: for each target, the bin holding its rank; prefix and rank are
-// narrowed to that bin.  After the last pass the key is complete.
-__global__ void radix_pick_kernel(Select* sel, unsigned* hist, int pass) {
-  const int t = threadIdx.x;
-  if (t < kTargets) {
-    const unsigned nbins = digit_mask(pass) + 1u;
-    const unsigned* hb = hist + t * kRadixBins;
-    long long r = sel->rank[t];
-    unsigned bin = 0;
-    for (; bin < nbins; bin++) {
-      if (r < (long long)hb[bin]) break;
-      r -= hb[bin];
+// One block of kRadixBins / 2 threads: for each target, the bin holding its
+// rank (block-wide exclusive scan of the histogram, each thread owning two
+// consecutive bins); prefix and rank are narrowed to that bin.  After the
+// last pass the key is complete.  Clears the histograms for the next pass.
+constexpr int kPickThreads = kRadixBins / 2;
+__global__ void __launch_bounds__(kPickThreads) radix_pick_kernel(Select* sel, unsigned* hist, int pass) {
+  __shared__ unsigned long long warp_tot[kPickThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned nbins = digit_mask(pass) + 1u;
+  const int width = pass == 2 ? 10 : 11;
+  for (int t = 0; t < kTargets; t++) {
+    unsigned* hb = hist + t * kRadixBins;
+    const unsigned c0 = 2 * tid < (int)nbins ? hb[2 * tid] : 0u;
+    const unsigned c1 = 2 * tid + 1 < (int)nbins ? hb[2 * tid + 1] : 0u;
+    // inclusive scan of the pair sums within the warp, then across warps
+    unsigned long long x = (unsigned long long)c0 + c1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
     }
-    if (bin >= nbins) bin = nbins - 1;  // not reached for a valid rank
-    const int width = pass == 2 ? 10 : 11;
-    sel->prefix[t] = (sel->prefix[t] << width) | bin;
-    sel->rank[t] = r;
-    if (pass == 2) sel->value[t] = key_value(sel->prefix[t]);
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    unsigned long long before = 0;
+    for (int i = 0; i < warp; i++) before += warp_tot[i];
+    const unsigned long long incl = before + x;
+    const unsigned long long excl = incl - c0 - c1;
+    const long long r = sel->rank[t];
+    __syncthreads();  // every thread has read rank[t] and warp_tot before they change
+    if ((long long)excl <= r && r < (long long)incl) {
+      const bool first = r < (long long)(excl + c0);
+      const unsigned bin = 2 * tid + (first ? 0u : 1u);
+      sel->prefix[t] = (sel->prefix[t] << width) | bin;
+      sel->rank[t] = r - (long long)(first ? excl : excl + c0);
+      if (pass == 2) sel->value[t] = key_value(sel->prefix[t]);
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < kTargets * kRadixBins; i += blockDim.x) hist[i] = 0u;
+  for (int i = tid; i < kTargets * kRadixBins; i += kPickThreads) hist[i] = 0u;
 }
 
 __global__ void finish_kernel(Select* sel, const double* __restrict__ oct_sums, const float* __restrict__ v,
@@ -390,10 +459,11 @@ __global__ void replace_kernel(const float* __restrict__ src, float* __restrict_
   for (int f = threadIdx.x; f < nf; f += blockDim.x) E[ascan_of(w, fast_axis, b, f)] = src[ascan_of(w, fast_axis, best, f)];
 }
 
+// One element (or A-scan) per thread (warp) up to the grid limit.
 inline unsigned grid_for(int64_t n, int per = kT) {
   int64_t b = (n + per - 1) / per;
   if (b < 1) b = 1;
-  if (b > 152 * 64) b = 152 * 64;
+  if (b > 0x7fffffff) b = 0x7fffffff;
   return (unsigned)b;
 }
 
@@ -417,7 +487,7 @@ extern "C" int octmc_saccade_validity(const float* octa, int w, int h, int d, in
   double* sums = nullptr;
   try {
     ck(cudaMallocAsync(&sums, sizeof(double) * nb, st));
-    bscan_sum_kernel<<<nb, kT, 0, st>>>(octa, w, h, d, fast_axis, sums);
+    bscan_sum_kernel<<<nb, kSumThreads, 0, st>>>(octa, w, h, d, fast_axis, sums);
     ck(cudaGetLastError());
     validity_kernel<<<1, 1024, 0, st>>>(sums, nb, (double)nf * d, v, means);
     ck(cudaGetLastError());
@@ -438,7 +508,7 @@ extern "C" int octmc_enface(const float* octa, const float* oct, int w, int h, i
   if (!(q_lo >= 0.0 && q_lo <= 1.0 && q_hi >= 0.0 && q_hi <= 1.0) || !std::isfinite(thresh))
     return OCTMC_ERR_INVALID_ARG;
   const int nb = fast_axis == 0 ? h : w, nf = fast_axis == 0 ? w : h;
-  if (nf > kMaxFast) return OCTMC_ERR_UNSUPPORTED;
+  if (nf > kMaxFast || h > 65535 || (w + 7) / 8 > 65535) return OCTMC_ERR_UNSUPPORTED;
   const cudaStream_t st = (cudaStream_t)stream;
   const int64_t nvox = (int64_t)w * h * d, nasc = (int64_t)w * h;
   // validity is needed on the host for the selected-voxel count
@@ -478,22 +548,25 @@ extern "C" int octmc_enface(const float* octa, const float* oct, int w, int h, i
     ck(cudaMemsetAsync(hist, 0, sizeof(unsigned) * kTargets * kRadixBins, st));
     ck(cudaMemsetAsync(kept, 0, sizeof(unsigned long long), st));
     // filters
-    median3_kernel<<<grid_for(nvox), kT, 0, st>>>(octa, w, h, d, m3);
+    const dim3 sb(kSx, kSy), sg((unsigned)((d + kSx - 1) / kSx), (unsigned)((w + kSy - 1) / kSy), (unsigned)h);
+    median3_kernel<<<sg, sb, 0, st>>>(octa, w, h, d, m3);
     ck(cudaGetLastError());
-    rank15_kernel<<<grid_for(nvox), kT, 0, st>>>(m3, w, h, d, fast_axis, r1);
+    rank15_kernel<<<sg, sb, 0, st>>>(m3, w, h, d, fast_axis, r1);
     ck(cudaGetLastError());
-    rank15_kernel<<<grid_for(nvox), kT, 0, st>>>(r1, w, h, d, 1 - fast_axis, r2);
+    rank15_kernel<<<sg, sb, 0, st>>>(r1, w, h, d, 1 - fast_axis, r2);
     ck(cudaGetLastError());
     // percentiles of the filtered voxels of the valid B-scans
     for (int pass = 0; pass < 3; pass++) {
-      radix_hist_kernel<<<grid_for(nvox), kT, 0, st>>>(r2, w, h, d, fast_axis, v, any, sel, pass, hist);
+      // streaming, no reuse: a resident-size grid, each block one shared histogram
+      const unsigned hb = (unsigned)std::min<int64_t>((nvox / kRun + kT) / kT, 152 * 8);
+      radix_hist_kernel<<<hb, kT, 0, st>>>(r2, w, h, d, fast_axis, v, any, sel, pass, hist);
       ck(cudaGetLastError());
-      radix_pick_kernel<<<1, 256, 0, st>>>(sel, hist, pass);
+      radix_pick_kernel<<<1, kPickThreads, 0, st>>>(sel, hist, pass);
       ck(cudaGetLastError());
     }
     // OCT threshold from the per-B-scan OCT sums, cut, projection
     if (std::isnan(t_oct)) {
-      bscan_sum_kernel<<<nb, kT, 0, st>>>(oct, w, h, d, fast_axis, osum);
+      bscan_sum_kernel<<<nb, kSumThreads, 0, st>>>(oct, w, h, d, fast_axis, osum);
       ck(cudaGetLastError());
     }
     finish_kernel<<<1, 32, 0, st>>>(sel, osum, v, nb, any, (double)nf * d, thresh, t_oct);
