@@ -571,7 +571,7 @@ typedef struct {
     double f;
 } oracle_stats;
 
-/* Minimises the level objective from x (in/out), eta fixed in P.
+/* Minimises fg (objective and gradient of n values) from x (in/out).
  * Line search (weak Wolfe, bisection/doubling): start at a = 1, or at
  * a = 1/||g||_2 when the history is empty; a trial that fails the Armijo
  * test (c1 = 1e-4) or is not finite halves the bracket; one that passes it
@@ -582,10 +582,11 @@ typedef struct {
  * (status 2).  Other stops: max|g| <= gtol (status 0), a relative decrease
  * (f_old - f_new) / max(|f_old|, |f_new|, 1) below ftol for 3 iterations in
  * a row (status 0), max_iter iterations (status 1). */
-int oracle_solve_level(const oracle_level *P, double *x, const oracle_solver *opt,
-                       oracle_stats *st)
+typedef void (*oracle_fg)(void *ctx, const double *x, double *f, double *g);
+
+static int lbfgs_minimize(long n, double *x, oracle_fg fg, void *ctx, const oracle_solver *opt,
+                          oracle_stats *st)
 {
-    const long n = 6L * P->w * P->h;
     const int m = opt->m > 0 ? (opt->m < 64 ? opt->m : 64) : 1;
     const size_t nb = sizeof(double) * (size_t)n;
     double *g = (double *)malloc(nb), *gt = (double *)malloc(nb), *xt = (double *)malloc(nb);
@@ -599,7 +600,7 @@ int oracle_solve_level(const oracle_level *P, double *x, const oracle_solver *op
     }
     int k = 0, head = 0, evals = 0, iters = 0, status = 1, small = 0, retried = 0;
     double f;
-    oracle_eval(P, x, &f, g, NULL);
+    fg(ctx, x, &f, g);
     evals++;
     while (iters < opt->max_iter) {
         double gmax = 0;
@@ -622,7 +623,7 @@ int oracle_solve_level(const oracle_level *P, double *x, const oracle_solver *op
         int accepted = 0, have_lo = 0;
         for (int ls = 0; ls < opt->max_ls; ls++) {
             for (long i = 0; i < n; i++) xt[i] = x[i] + a * dir[i];
-            oracle_eval(P, xt, &ft, gt, NULL);
+            fg(ctx, xt, &ft, gt);
             evals++;
             double dgt = dot(gt, dir, n);
             if (!(ft <= f + 1e-4 * a * dg0)) {
@@ -692,6 +693,19 @@ int oracle_solve_level(const oracle_level *P, double *x, const oracle_solver *op
     st->status = status;
     st->f = f;
     return 0;
+}
+
+static void level_fg(void *ctx, const double *x, double *f, double *g)
+{
+    oracle_eval((const oracle_level *)ctx, x, f, g, NULL);
+}
+
+/* Minimises the level objective from x (in/out), eta fixed in P (the
+ * minimiser above on oracle_eval). */
+int oracle_solve_level(const oracle_level *P, double *x, const oracle_solver *opt,
+                       oracle_stats *st)
+{
+    return lbfgs_minimize(6L * P->w * P->h, x, level_fg, (void *)P, opt, st);
 }
 
 /* Number of threads the OpenMP loops use (1 without OpenMP). */
@@ -804,4 +818,120 @@ void oracle_merge(const oracle_level *P, const double *disp, double beta, double
             }
         }
     free(map);
+}
+
+/* ------------------------------------------------------------------ */
+/* Rough axial prealignment (stage 1, Sec. 2.1 / Fig. 1).               */
+/* Readings (the paper gives the parameterisation in words and defers  */
+/* the tilt term T to earlier work):                                    */
+/*  - parameters per B-scan b of each scan: axial offset a_b and tilt   */
+/*    t_b; the A-scan at fast-axis position f of B-scan b is displaced  */
+/*    axially by a_b + t_b (f - c), c = (n_f - 1) / 2, transversally by */
+/*    0.  Layout [aX(h), tX(h), aY(w), tY(w)]: X-fast B-scans are rows  */
+/*    j (f = i), Y-fast B-scans columns i (f = j);                      */
+/*  - objective S_0^str + alpha R + M + T (Eq. 1): the structural data  */
+/*    term alone (no angiography: delta_0 = 0, eta = 1), R and M of the */
+/*    induced field;                                                    */
+/*  - T fixes the two tilt modes the data cannot see (a common tilt of  */
+/*    the frame shows as equal tilts of one scan's B-scans and offsets  */
+/*    linear in b of the other's):                                      */
+/*    T = (sum_b tX_b)^2 / (2 h) + (sum_b tY_b)^2 / (2 w);              */
+/*  - between levels: fine B-scan b sits at (b - 1/2) / 2 on the coarse */
+/*    level (clamped, linear); offsets double, tilts are kept.          */
+/* ------------------------------------------------------------------ */
+void oracle_prealign_disp(const oracle_level *P, const double *prm, double *disp)
+{
+    const int w = P->w, h = P->h;
+    const double cx = 0.5 * (w - 1), cy = 0.5 * (h - 1);
+    const double *aX = prm, *tX = prm + h, *aY = prm + 2 * h, *tY = prm + 2 * h + w;
+    memset(disp, 0, sizeof(double) * 6 * (size_t)w * h);
+    for (int j = 0; j < h; j++)
+        for (int i = 0; i < w; i++) {
+            disp[didx(w, h, 0, 2, i, j)] = aX[j] + tX[j] * (i - cx);
+            disp[didx(w, h, 1, 2, i, j)] = aY[i] + tY[i] * (j - cy);
+        }
+}
+
+/* f and df/dprm of the stage-1 objective; terms (may be NULL) receives
+ * [S^str, R, M, T, f]. */
+void oracle_prealign_eval(const oracle_level *P, const double *prm, double *f_out, double *gprm, double *terms)
+{
+    const int w = P->w, h = P->h;
+    const double cx = 0.5 * (w - 1), cy = 0.5 * (h - 1);
+    oracle_level Q = *P;
+    Q.delta0 = 0.0;
+    Q.eta = 1.0;
+    const size_t n = 6 * (size_t)w * h;
+    double *disp = (double *)malloc(sizeof(double) * n), *g = (double *)malloc(sizeof(double) * n);
+    double t6[6], f;
+    oracle_prealign_disp(P, prm, disp);
+    oracle_eval(&Q, disp, &f, g, t6);
+    const double *tX = prm + h, *tY = prm + 2 * h + w;
+    double sX = 0.0, sY = 0.0;
+    for (int j = 0; j < h; j++) sX += tX[j];
+    for (int i = 0; i < w; i++) sY += tY[i];
+    const double T = sX * sX / (2.0 * h) + sY * sY / (2.0 * w);
+    f += T;
+    if (gprm) {
+        for (int j = 0; j < h; j++) {
+            double ga = 0.0, gt = 0.0;
+            for (int i = 0; i < w; i++) {
+                const double gz = g[didx(w, h, 0, 2, i, j)];
+                ga += gz;
+                gt += gz * (i - cx);
+            }
+            gprm[j] = ga;
+            gprm[h + j] = gt + sX / h;
+        }
+        for (int i = 0; i < w; i++) {
+            double ga = 0.0, gt = 0.0;
+            for (int j = 0; j < h; j++) {
+                const double gz = g[didx(w, h, 1, 2, i, j)];
+                ga += gz;
+                gt += gz * (j - cy);
+            }
+            gprm[2 * h + i] = ga;
+            gprm[2 * h + w + i] = gt + sY / w;
+        }
+    }
+    if (terms) {
+        terms[0] = t6[0];
+        terms[1] = t6[2];
+        terms[2] = t6[3];
+        terms[3] = T;
+        terms[4] = f;
+    }
+    if (f_out) *f_out = f;
+    free(disp);
+    free(g);
+}
+
+static void prealign_fg(void *ctx, const double *x, double *f, double *g)
+{
+    oracle_prealign_eval((const oracle_level *)ctx, x, f, g, NULL);
+}
+
+/* L-BFGS solve of the stage-1 objective of one level from prm (in/out). */
+int oracle_prealign_level(const oracle_level *P, double *prm, const oracle_solver *opt, oracle_stats *st)
+{
+    return lbfgs_minimize(2L * (P->w + P->h), prm, prealign_fg, (void *)P, opt, st);
+}
+
+/* Parameters of the coarse level (wc, hc) to the fine level (wf, hf). */
+void oracle_prealign_prolong(const double *pc, int wc, int hc, double *pf, int wf, int hf)
+{
+    for (int part = 0; part < 4; part++) {
+        const int nc = part < 2 ? hc : wc, nf = part < 2 ? hf : wf;
+        const double *c = pc + (part < 2 ? part * hc : 2 * hc + (part - 2) * wc);
+        double *o = pf + (part < 2 ? part * hf : 2 * hf + (part - 2) * wf);
+        const double scale = (part % 2 == 0) ? 2.0 : 1.0;  /* offsets double, tilts are kept */
+        for (int b = 0; b < nf; b++) {
+            double x = 0.5 * b - 0.25;
+            if (x < 0) x = 0;
+            if (x > nc - 1) x = nc - 1;
+            const int x0 = (int)floor(x), x1 = x0 + 1 < nc ? x0 + 1 : x0;
+            const double fx = x - x0;
+            o[b] = scale * ((1.0 - fx) * c[x0] + fx * c[x1]);
+        }
+    }
 }

@@ -92,6 +92,11 @@ def _load():
         lib.oracle_solve_level.restype = C.c_int
         lib.oracle_num_threads.restype = C.c_int
         lib.oracle_merge.argtypes = [C.POINTER(_Level), _dp, C.c_double, C.c_double] + [C.c_void_p] * 5 + [C.c_void_p]
+        lib.oracle_prealign_disp.argtypes = [C.POINTER(_Level), _dp, _dp]
+        lib.oracle_prealign_eval.argtypes = [C.POINTER(_Level), _dp, C.POINTER(C.c_double), C.c_void_p, C.c_void_p]
+        lib.oracle_prealign_level.argtypes = [C.POINTER(_Level), _dp, C.POINTER(_Solver), C.POINTER(_Stats)]
+        lib.oracle_prealign_level.restype = C.c_int
+        lib.oracle_prealign_prolong.argtypes = [_dp, C.c_int, C.c_int, _dp, C.c_int, C.c_int]
         lib.oracle_saccade_validity.argtypes = [_fp, C.c_int, C.c_int, C.c_int, C.c_int, _fp, _dp]
         lib.oracle_median3.argtypes = [_fp, C.c_int, C.c_int, C.c_int, _fp]
         lib.oracle_rank_filter.argtypes = [_fp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _fp]
@@ -186,6 +191,12 @@ def pyramid_time(t):
     h, w = t.shape
     out = np.zeros((_half(h), _half(w)))
     _load().oracle_pyramid_time(t, w, h, out)
+    return out
+
+
+def prealign_prolong(prm, wc, hc, wf, hf):
+    out = np.zeros(2 * (wf + hf))
+    _load().oracle_prealign_prolong(np.ascontiguousarray(prm, dtype=np.float64), wc, hc, out, wf, hf)
     return out
 
 
@@ -317,6 +328,56 @@ class OracleProblem:
         p.vy = None if self.vy is None else pyramid_line(self.vy)
         p.eta = 1.0
         return p
+
+    # -- rough axial prealignment (stage 1): parameters [aX(h), tX(h), aY(w), tY(w)]
+    def n_prealign(self):
+        return 2 * (self.h + self.w)
+
+    def prealign_disp(self, prm):
+        """The displacement field [2][3][h][w] the B-scan offsets and tilts induce."""
+        prm = np.ascontiguousarray(prm, dtype=np.float64)
+        assert prm.shape == (self.n_prealign(),)
+        out = np.zeros(self.shape_disp())
+        L = self._level()
+        _load().oracle_prealign_disp(C.byref(L), prm, out)
+        return out
+
+    def prealign_eval(self, prm, grad=True):
+        """(f, gradient or None, terms [S^str, R, M, T, f]) of the stage-1 objective."""
+        prm = np.ascontiguousarray(prm, dtype=np.float64)
+        assert prm.shape == (self.n_prealign(),)
+        L = self._level()
+        f = C.c_double()
+        g = np.zeros(self.n_prealign()) if grad else None
+        terms = np.zeros(5)
+        _load().oracle_prealign_eval(C.byref(L), prm, C.byref(f), None if g is None else g.ctypes.data,
+                                     terms.ctypes.data)
+        return f.value, g, terms
+
+    def prealign_level(self, prm, m=8, max_iter=200, max_ls=20, gtol=1e-6, ftol=1e-9):
+        x = np.array(prm, dtype=np.float64, order="C", copy=True)
+        L = self._level()
+        opt = _Solver(m, max_iter, max_ls, gtol, ftol)
+        st = _Stats()
+        _load().oracle_prealign_level(C.byref(L), x, C.byref(opt), C.byref(st))
+        return x, dict(iters=st.iters, evals=st.evals, status=st.status, f=st.f)
+
+    def prealign_full(self, levels, **kw):
+        """Coarse-to-fine stage-1 solve from zero parameters."""
+        pyr = self.pyramid(levels)
+        prm = np.zeros(pyr[-1].n_prealign())
+        stats = []
+        for lv in range(levels - 1, -1, -1):
+            P = pyr[lv]
+            if lv != levels - 1:
+                C_ = pyr[lv + 1]
+                fine = np.zeros(P.n_prealign())
+                _load().oracle_prealign_prolong(np.ascontiguousarray(prm), C_.w, C_.h, fine, P.w, P.h)
+                prm = fine
+            prm, st = P.prealign_level(prm, **kw)
+            st["level"] = lv
+            stats.append(st)
+        return prm, stats
 
     def pyramid(self, levels):
         out = [self]
