@@ -169,6 +169,45 @@ int octmc_merge(octmc_problem *p, const double *disp0_dev, double beta, double t
                 float *corrected_x, float *corrected_y, float *weights, float *angio);
 
 /* ---------------------------------------------------------------------
+ * Rough axial prealignment (stage 1 of Sec. 2.1: "only estimates axial
+ * displacements and tilt at B-scan granularity").  Parameters of a level
+ * with w x h A-scans, device float64 [aX(h), tX(h), aY(w), tY(w)]: the
+ * X-fast B-scan j (a row) moves A-scan (i, j) axially by
+ * aX_j + tX_j (i - (w-1)/2), the Y-fast B-scan i (a column) by
+ * aY_i + tY_i (j - (h-1)/2); transverse displacements are 0.  Objective:
+ * S_0^str + alpha R + M + T (Eq. 1), the structural term alone (delta_0 = 0,
+ * eta = 1) on the induced field, and the tilt term T, which fixes the three
+ * deformations of the common frame the data cannot see (a common x tilt,
+ * y tilt and x y twist), each weighted like M for the same displacement
+ * energy: T = 2 w vx sX^2 / h + 2 h vy sY^2 / w + 2 w h vx vy sT^2 / nT^2,
+ * vx = (w^2-1)/12, vy = (h^2-1)/12, sX = sum tX, sY = sum tY,
+ * sT = sum_j tX_j (j - cy) + sum_i tY_i (i - cx), nT = h vy + w vx (the
+ * paper defers T's form to earlier work).  The solver is the 3-D solve's L-BFGS
+ * with the same line search, limits and history length.
+ * --------------------------------------------------------------------- */
+
+/* The field [2][3][h][w] (device) induced by the parameters of `level`. */
+int octmc_prealign_disp(octmc_problem *p, int level, const double *prm_dev, double *disp_dev);
+
+/* Stage-1 objective at prm_dev: *f_host (host, may be NULL) and its
+ * gradient grad_prm_dev (device, 2 (w + h) values, may be NULL).
+ * Errors: INVALID_ARG, CUDA, NONFINITE. */
+int octmc_prealign_eval(octmc_problem *p, int level, const double *prm_dev, double *f_host,
+                        double *grad_prm_dev);
+
+/* L-BFGS solve of the stage-1 objective of one level from prm_inout_dev
+ * (overwritten).  Returns OK, NOT_CONVERGED (iteration cap) or an error. */
+int octmc_prealign_level(octmc_problem *p, int level, double *prm_inout_dev, octmc_stats *st);
+
+/* Coarse-to-fine stage-1 solve from zero parameters: between levels fine
+ * B-scan b takes the coarse parameters at (b - 1/2)/2 (clamped, linear),
+ * offsets doubled, tilts kept.  prm_out_dev (device, 2 (w + h) of level 0)
+ * receives the level-0 parameters, disp0_out_dev (device, may be NULL) the
+ * induced level-0 field; st (host, may be NULL) `levels` entries, coarse
+ * to fine. */
+int octmc_prealign_full(octmc_problem *p, double *prm_out_dev, double *disp0_out_dev, octmc_stats *st);
+
+/* ---------------------------------------------------------------------
  * Angiography preprocessing of one scan (inputs of the objective).
  * Volumes are device float32 [h][w][d] (depth contiguous) on the common
  * grid; fast_axis 0: X-fast scan, B-scans are the rows j (h of them);

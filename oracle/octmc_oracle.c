@@ -832,10 +832,19 @@ void oracle_merge(const oracle_level *P, const double *disp, double beta, double
 /*  - objective S_0^str + alpha R + M + T (Eq. 1): the structural data  */
 /*    term alone (no angiography: delta_0 = 0, eta = 1), R and M of the */
 /*    induced field;                                                    */
-/*  - T fixes the two tilt modes the data cannot see (a common tilt of  */
-/*    the frame shows as equal tilts of one scan's B-scans and offsets  */
-/*    linear in b of the other's):                                      */
-/*    T = (sum_b tX_b)^2 / (2 h) + (sum_b tY_b)^2 / (2 w);              */
+/*  - T fixes the tilt modes the data cannot see.  A deformation of the */
+/*    common frame z = f(x, y) that both parameterisations can express  */
+/*    (f in span{1, x, y, x y}) leaves the objective unchanged; M fixes */
+/*    the constant, T the other three: a common x tilt (equal tilts of  */
+/*    the X-fast B-scans, Y-fast offsets linear in i), a common y tilt, */
+/*    and the twist x y (X tilts linear in j, Y tilts linear in i).     */
+/*    Each term is the square of the linear functional the mode moves,  */
+/*    weighted so that a mode of the frame costs what M charges for a   */
+/*    shift of the same displacement energy (both volumes' squared      */
+/*    displacements, 2 w h c^2 for a shift c).  With vx = (w^2 - 1)/12, */
+/*    vy = (h^2 - 1)/12, sX = sum tX, sY = sum tY,                      */
+/*    sT = sum_j tX_j (j - cy) + sum_i tY_i (i - cx), nT = h vy + w vx:  */
+/*    T = 2 w vx sX^2 / h + 2 h vy sY^2 / w + 2 w h vx vy sT^2 / nT^2.  */
 /*  - between levels: fine B-scan b sits at (b - 1/2) / 2 on the coarse */
 /*    level (clamped, linear); offsets double, tilts are kept.          */
 /* ------------------------------------------------------------------ */
@@ -867,10 +876,21 @@ void oracle_prealign_eval(const oracle_level *P, const double *prm, double *f_ou
     oracle_prealign_disp(P, prm, disp);
     oracle_eval(&Q, disp, &f, g, t6);
     const double *tX = prm + h, *tY = prm + 2 * h + w;
-    double sX = 0.0, sY = 0.0;
-    for (int j = 0; j < h; j++) sX += tX[j];
-    for (int i = 0; i < w; i++) sY += tY[i];
-    const double T = sX * sX / (2.0 * h) + sY * sY / (2.0 * w);
+    double sX = 0.0, sY = 0.0, sT = 0.0, nT = 0.0;
+    for (int j = 0; j < h; j++) {
+        sX += tX[j];
+        sT += tX[j] * (j - cy);
+        nT += (j - cy) * (j - cy);
+    }
+    for (int i = 0; i < w; i++) {
+        sY += tY[i];
+        sT += tY[i] * (i - cx);
+        nT += (i - cx) * (i - cx);
+    }
+    const double vx = (w * (double)w - 1.0) / 12.0, vy = (h * (double)h - 1.0) / 12.0;
+    const double lx = 2.0 * w * vx / h, ly = 2.0 * h * vy / w;
+    const double lt = nT > 0 ? 2.0 * w * h * vx * vy / (nT * nT) : 0.0;
+    const double T = lx * sX * sX + ly * sY * sY + lt * sT * sT;
     f += T;
     if (gprm) {
         for (int j = 0; j < h; j++) {
@@ -881,7 +901,7 @@ void oracle_prealign_eval(const oracle_level *P, const double *prm, double *f_ou
                 gt += gz * (i - cx);
             }
             gprm[j] = ga;
-            gprm[h + j] = gt + sX / h;
+            gprm[h + j] = gt + 2.0 * lx * sX + 2.0 * lt * sT * (j - cy);
         }
         for (int i = 0; i < w; i++) {
             double ga = 0.0, gt = 0.0;
@@ -891,7 +911,7 @@ void oracle_prealign_eval(const oracle_level *P, const double *prm, double *f_ou
                 gt += gz * (j - cy);
             }
             gprm[2 * h + i] = ga;
-            gprm[2 * h + w + i] = gt + sY / w;
+            gprm[2 * h + w + i] = gt + 2.0 * ly * sY + 2.0 * lt * sT * (i - cx);
         }
     }
     if (terms) {

@@ -179,6 +179,54 @@ class Problem:
                 "octmc_level_data")
         return out
 
+    # -- rough axial prealignment (stage 1): parameters [aX(h), tX(h), aY(w), tY(w)] float64
+    def prealign_size(self, level=0):
+        w, h, _ = self.level_shape(level)
+        return 2 * (w + h)
+
+    def _check_prm(self, t, level):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+                and t.numel() >= self.prealign_size(level)):
+            raise ValueError("prealignment parameters must be a contiguous float64 CUDA tensor of %d values"
+                             % self.prealign_size(level))
+
+    def prealign_disp(self, level, prm):
+        """``octmc_prealign_disp``: the induced field [2][3][h][w]."""
+        self._check_prm(prm, level)
+        out = self.zeros(level)
+        N.check(N.lib().octmc_prealign_disp(self._h, level, _ptr(prm), _ptr(out)), "octmc_prealign_disp")
+        return out
+
+    def prealign_eval(self, level, prm, grad=None):
+        """``octmc_prealign_eval``: f of the stage-1 objective (gradient into ``grad``)."""
+        self._check_prm(prm, level)
+        if grad is not None:
+            self._check_prm(grad, level)
+        f = C.c_double()
+        N.check(N.lib().octmc_prealign_eval(self._h, level, _ptr(prm), C.byref(f), _ptr(grad)),
+                "octmc_prealign_eval")
+        return f.value
+
+    def prealign_level(self, level, prm):
+        """``octmc_prealign_level``: solve one level in place; returns the stats dict."""
+        self._check_prm(prm, level)
+        st = N.Stats()
+        rc = N.check(N.lib().octmc_prealign_level(self._h, level, _ptr(prm), C.byref(st)), "octmc_prealign_level")
+        out = st.as_dict()
+        out["rc"] = rc
+        return out
+
+    def prealign_full(self, want_disp=True):
+        """``octmc_prealign_full``: (level-0 parameters, induced level-0 field or None, per-level stats)."""
+        prm = torch.zeros(self.prealign_size(0), dtype=torch.float64, device="cuda")
+        disp = self.zeros(0) if want_disp else None
+        st = (N.Stats * self.levels)()
+        rc = N.check(N.lib().octmc_prealign_full(self._h, _ptr(prm), _ptr(disp), st), "octmc_prealign_full")
+        stats = [s.as_dict() for s in st]
+        for s in stats:
+            s["rc"] = rc
+        return prm, disp, stats
+
     def merge(self, disp0, beta=2.0, tau=0.05, outputs=("merged", "weights", "angio"), out=None):
         """``octmc_merge``: final resampling and merging at level 0 (Sec. 2.1, 2.5).
 

@@ -54,6 +54,10 @@ _SIGS = {
     "octmc_prolong": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "octmc_level_data": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 6),
     "octmc_merge": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double] + [C.c_void_p] * 5),
+    "octmc_prealign_disp": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "octmc_prealign_eval": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
+    "octmc_prealign_level": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(Stats)]),
+    "octmc_prealign_full": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Stats)]),
     "octmc_saccade_validity": (C.c_int, [C.c_void_p] + [C.c_int] * 4 + [C.c_void_p] * 3),
     "octmc_enface": (C.c_int, [C.c_void_p, C.c_void_p] + [C.c_int] * 4 + [C.c_void_p] + [C.c_double] * 4
                      + [C.c_void_p] * 4),

@@ -337,6 +337,13 @@ struct octmc_problem {
   double* dir = nullptr;
   octmc_lbfgs* opt = nullptr;
   unsigned long long* mcounts = nullptr;  // merge: fixed-point density maps [2][h][w]
+  // prealignment: induced field and its gradient (level-0 sized), and
+  // [T, g . dir] on the device and its pinned host copy
+  double* pre_D = nullptr;
+  double* pre_G = nullptr;
+  double* pre_aux = nullptr;
+  double* pre_aux_host = nullptr;
+  double* pre_prm = nullptr;  // 2 (w + h) of level 0: parameter gradient scratch / coarse copy
   std::vector<void*> temps;  // float32 pyramid copies while building 16-bit storage
   // optional CUDA-event timing of the data-term kernel (octmc_profile_*)
   bool profile = false;
@@ -360,6 +367,8 @@ struct octmc_problem {
     if (res_host) cudaFreeHost(res_host);
     dfree(x); dfree(g); dfree(xt); dfree(gt); dfree(xb); dfree(gb); dfree(dir);
     dfree(mcounts);
+    dfree(pre_D); dfree(pre_G); dfree(pre_aux); dfree(pre_prm);
+    if (pre_aux_host) cudaFreeHost(pre_aux_host);
     delete opt;
   }
 
@@ -868,6 +877,135 @@ int solve_impl(octmc_problem* P, int l, double* disp_inout, octmc_stats* st) {
   return rc;
 }
 
+// ------------------------------------------------------------ prealignment
+// Stage 1 of Sec. 2.1: L-BFGS over the per-B-scan axial offsets and tilts
+// (2 (w + h) values per level), with the same line search and stopping rules
+// as the 3-D solve; each evaluation maps the parameters to the field, runs
+// the objective with the structural term alone (delta_0 = 0, eta = 1) and
+// reduces the field gradient to the parameters.
+int prealign_n(const octmc_problem* P, int l) { return 2 * (P->lv[l].dev.w + P->lv[l].dev.h); }
+
+void ensure_prealign(octmc_problem* P) {
+  ensure_solver(P);
+  if (P->pre_D) return;
+  const size_t n = (size_t)6 * P->plane(0);
+  P->pre_D = dalloc<double>(n);
+  P->pre_G = dalloc<double>(n);
+  P->pre_aux = dalloc<double>(2);
+  P->pre_prm = dalloc<double>((size_t)prealign_n(P, 0));
+  CK(cudaMallocHost(&P->pre_aux_host, 2 * sizeof(double)));
+}
+
+// f (host) and, if gprm, the parameter gradient (device); with dir also
+// gprm . dir in *gdir.
+void prealign_eval_impl(octmc_problem* P, int l, const double* prm, double* gprm, const double* dir, double* f,
+                        double* gdir) {
+  ensure_prealign(P);
+  const LevelDev& L = P->lv[l].dev;
+  CK(launch_prm_to_disp(prm, L.w, L.h, P->pre_D, P->st));
+  eval_batch(P->st, {EvalReq{P, l, P->pre_D, gprm ? P->pre_G : nullptr, nullptr, 1.0, 0.0}});
+  if (gprm) {
+    CK(launch_grad_to_prm(P->pre_G, L.w, L.h, prm, gprm, P->pre_aux, P->st));
+    if (dir) CK(launch_prm_dot(gprm, dir, prealign_n(P, l), P->pre_aux + 1, P->st));
+  } else {
+    // T alone: reduce a zero field gradient into scratch
+    CK(cudaMemsetAsync(P->pre_G, 0, sizeof(double) * 6 * P->plane(l), P->st));
+    CK(launch_grad_to_prm(P->pre_G, L.w, L.h, prm, P->pre_prm, P->pre_aux, P->st));
+  }
+  CK(cudaMemcpyAsync(P->pre_aux_host, P->pre_aux, 2 * sizeof(double), cudaMemcpyDeviceToHost, P->st));
+  CK(cudaStreamSynchronize(P->st));
+  *f = P->res_host->terms[4] + P->pre_aux_host[0];
+  if (gdir) *gdir = P->pre_aux_host[1];
+}
+
+int prealign_level_impl(octmc_problem* P, int l, double* prm, octmc_stats* st) {
+  ensure_prealign(P);
+  const auto t0 = std::chrono::steady_clock::now();
+  const octmc_desc& D = P->desc;
+  const int n = prealign_n(P, l);
+  octmc_lbfgs* O = P->opt;
+  O->n = n;
+  O->reset();
+  double *x = P->x, *g = P->g, *xt = P->xt, *gt = P->gt, *xb = P->xb, *gb = P->gb, *dir = P->dir;
+  CK(cudaMemcpyAsync(x, prm, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->st));
+  double f;
+  prealign_eval_impl(P, l, x, g, nullptr, &f, nullptr);
+  int evals = 1, iters = 0, status = 1, small = 0, retried = 0;
+  O->prepare(g, false);
+  while (iters < D.max_iter) {
+    if (O->gmax <= D.gtol) {
+      status = 0;
+      break;
+    }
+    const double dg0 = O->direction(g, dir);
+    double a = (O->k() == 0) ? 1.0 / std::sqrt(O->gg) : 1.0;
+    double lo = 0.0, hi = std::numeric_limits<double>::infinity(), ft = 0.0, fb = 0.0;
+    bool accepted = false, have_lo = false;
+    for (int ls = 0; ls < D.max_ls; ls++) {
+      CK(launch_axpy(x, a, dir, xt, n, P->st));
+      double dgt;
+      prealign_eval_impl(P, l, xt, gt, dir, &ft, &dgt);
+      evals++;
+      if (!(ft <= f + 1e-4 * a * dg0)) {
+        hi = a;
+        a = 0.5 * (lo + hi);
+      } else if (dgt < 0.9 * dg0) {
+        lo = a;
+        have_lo = true;
+        fb = ft;
+        std::swap(xb, xt);
+        std::swap(gb, gt);
+        a = std::isinf(hi) ? 2.0 * a : 0.5 * (lo + hi);
+      } else {
+        accepted = true;
+        break;
+      }
+    }
+    if (!accepted) {
+      if (have_lo) {
+        std::swap(xt, xb);
+        std::swap(gt, gb);
+        ft = fb;
+      } else if (O->k() > 0 && !retried) {
+        O->reset();
+        retried = 1;
+        O->prepare(g, false);
+        continue;
+      } else {
+        status = 2;
+        break;
+      }
+    }
+    retried = 0;
+    CK(launch_sub2(xt, x, gt, g, O->S[O->spare], O->Y[O->spare], n, P->st));
+    const double rel = (f - ft) / std::max(std::max(std::fabs(f), std::fabs(ft)), 1.0);
+    std::swap(x, xt);
+    std::swap(g, gt);
+    f = ft;
+    iters++;
+    small = (rel < D.ftol) ? small + 1 : 0;
+    O->prepare(g, true);
+    if (small >= 3) {
+      status = 0;
+      break;
+    }
+  }
+  CK(cudaMemcpyAsync(prm, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->st));
+  CK(cudaStreamSynchronize(P->st));
+  if (st) {
+    *st = octmc_stats{};
+    st->level = l;
+    st->iters = iters;
+    st->evals = evals;
+    st->status = status;
+    st->f = f;
+    st->eta = 1.0;
+    st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (!std::isfinite(f)) return OCTMC_ERR_NONFINITE;
+  return status == 1 ? OCTMC_NOT_CONVERGED : OCTMC_OK;
+}
+
 template <typename F>
 int guarded(F&& f) {
   try {
@@ -1154,6 +1292,64 @@ int octmc_merge(octmc_problem* p, const double* disp0, double beta, double tau, 
     if (merged || cx || cy) CK(launch_resample_merge(L, disp0, wts, merged, cx, cy, p->st));
     CK(cudaStreamSynchronize(p->st));
     return OCTMC_OK;
+  });
+}
+
+int octmc_prealign_disp(octmc_problem* p, int level, const double* prm, double* disp) {
+  if (!valid_level(p, level) || !prm || !disp) return OCTMC_ERR_INVALID_ARG;
+  return guarded([&] {
+    const LevelDev& L = p->lv[level].dev;
+    CK(launch_prm_to_disp(prm, L.w, L.h, disp, p->st));
+    CK(cudaStreamSynchronize(p->st));
+    return OCTMC_OK;
+  });
+}
+
+int octmc_prealign_eval(octmc_problem* p, int level, const double* prm, double* f_host, double* grad_prm) {
+  if (!valid_level(p, level) || !prm) return OCTMC_ERR_INVALID_ARG;
+  return guarded([&] {
+    double f;
+    prealign_eval_impl(p, level, prm, grad_prm, nullptr, &f, nullptr);
+    if (f_host) *f_host = f;
+    return std::isfinite(f) ? OCTMC_OK : OCTMC_ERR_NONFINITE;
+  });
+}
+
+int octmc_prealign_level(octmc_problem* p, int level, double* prm_inout, octmc_stats* st) {
+  if (!valid_level(p, level) || !prm_inout) return OCTMC_ERR_INVALID_ARG;
+  return guarded([&] { return prealign_level_impl(p, level, prm_inout, st); });
+}
+
+int octmc_prealign_full(octmc_problem* p, double* prm_out, double* disp0_out, octmc_stats* st) {
+  if (!p || !prm_out) return OCTMC_ERR_INVALID_ARG;
+  return guarded([&] {
+    ensure_prealign(p);
+    const int L = (int)p->lv.size();
+    // the parameters of the current level live in the caller's buffer
+    // (level-0 sized); the coarse copy for the prolongation in pre_prm
+    double* cur = prm_out;
+    CK(cudaMemsetAsync(cur, 0, sizeof(double) * prealign_n(p, L - 1), p->st));
+    int rc = OCTMC_OK;
+    for (int l = L - 1; l >= 0; l--) {
+      if (l != L - 1) {
+        const LevelDev& C = p->lv[l + 1].dev;
+        const LevelDev& F = p->lv[l].dev;
+        double* tmp = p->pre_prm;
+        CK(cudaMemcpyAsync(tmp, cur, sizeof(double) * prealign_n(p, l + 1), cudaMemcpyDeviceToDevice, p->st));
+        CK(launch_prm_prolong(tmp, C.w, C.h, cur, F.w, F.h, p->st));
+      }
+      octmc_stats s{};
+      const int r = prealign_level_impl(p, l, cur, &s);
+      if (st) st[L - 1 - l] = s;
+      if (r < 0) return r;
+      if (r == OCTMC_NOT_CONVERGED) rc = r;
+    }
+    if (disp0_out) {
+      const LevelDev& F = p->lv[0].dev;
+      CK(launch_prm_to_disp(cur, F.w, F.h, disp0_out, p->st));
+      CK(cudaStreamSynchronize(p->st));
+    }
+    return rc;
   });
 }
 

@@ -245,6 +245,13 @@ cudaError_t launch_reg(const RegArgs& a, cudaStream_t s);
 int reg_grid_blocks(int64_t n_ascans);
 int msum_grid_blocks();
 
+// Rough axial prealignment (stage 1 of Sec. 2.1).
+cudaError_t launch_prm_to_disp(const double* prm, int w, int h, double* disp, cudaStream_t s);
+cudaError_t launch_grad_to_prm(const double* g, int w, int h, const double* prm, double* gprm, double* T_out,
+                               cudaStream_t s);
+cudaError_t launch_prm_dot(const double* a, const double* b, int n, double* out, cudaStream_t s);
+cudaError_t launch_prm_prolong(const double* pc, int wc, int hc, double* pf, int wf, int hf, cudaStream_t s);
+
 // Final resampling / merging (Sec. 2.1, 2.5).
 cudaError_t launch_resample_merge(const LevelDev& L, const double* disp, const float* weights, float* merged,
                                   float* cx, float* cy, cudaStream_t s);

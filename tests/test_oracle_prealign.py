@@ -18,6 +18,17 @@ def profile(z, d):
     return out.astype(np.float32)
 
 
+def unseen_free(tX, tY):
+    """Tilts with the three unseen modes (common x tilt, y tilt, twist)
+    projected out, so the tilt term does not bias their recovery."""
+    h, w = len(tX), len(tY)
+    oy, ox = np.arange(h) - 0.5 * (h - 1), np.arange(w) - 0.5 * (w - 1)
+    tX = tX - tX.mean()
+    tY = tY - tY.mean()
+    k = (tX @ oy + tY @ ox) / (oy @ oy + ox @ ox)
+    return tX - k * oy, tY - k * ox
+
+
 def render(w, h, d, zX, tX, zY, tY):
     k = np.arange(d, dtype=np.float64)
     cx, cy = 0.5 * (w - 1), 0.5 * (h - 1)
@@ -57,8 +68,25 @@ def test_tilt_term_closed_form():
     prm = np.zeros(P.n_prealign())
     prm[h:2 * h] = 0.03
     prm[2 * h + w:] = -0.01
+    # a common x tilt tau of the frame (X tilts tau, Y offsets tau (i - cx))
+    # costs what M charges for the same displacement energy: 2 w h tau^2 vx
+    vx, vy = (w * w - 1) / 12.0, (h * h - 1) / 12.0
     _, _, t = P.prealign_eval(prm)
-    assert t[3] == pytest.approx((0.03 * h) ** 2 / (2 * h) + (0.01 * w) ** 2 / (2 * w), rel=1e-14)
+    assert t[3] == pytest.approx(2 * w * h * (0.03 ** 2 * vx + 0.01 ** 2 * vy), rel=1e-13)
+    # the twist kappa (X tilts kappa (j - cy), Y tilts kappa (i - cx)):
+    # energy 2 w h kappa^2 vx vy
+    oy, ox = np.arange(h) - 0.5 * (h - 1), np.arange(w) - 0.5 * (w - 1)
+    prm[:] = 0.0
+    prm[h:2 * h] = 0.002 * oy
+    prm[2 * h + w:] = 0.002 * ox
+    _, _, t = P.prealign_eval(prm)
+    assert t[3] == pytest.approx(2 * w * h * 0.002 ** 2 * vx * vy, rel=1e-12)
+    # and M matches it for the induced displacements of a shift
+    prm[:] = 0.0
+    prm[:h] = 0.7
+    prm[2 * h:2 * h + w] = 0.7
+    _, _, t = P.prealign_eval(prm)
+    assert t[2] == pytest.approx(2 * w * h * 0.7 ** 2, rel=1e-12) and t[3] == 0.0
 
 
 def test_gradient_matches_central_differences():
@@ -93,8 +121,7 @@ def test_recovers_known_offsets_and_tilts():
     j, i = np.arange(h), np.arange(w)
     zX = 1.5 * np.sin(2 * np.pi * 0.6 * j / h) + 0.4
     zY = 1.2 * np.cos(2 * np.pi * 0.5 * i / w) - 0.3
-    tX = 0.03 * np.cos(2 * np.pi * j / h)  # zero mean: the tilt term does not bias it
-    tY = 0.02 * np.sin(2 * np.pi * i / w)
+    tX, tY = unseen_free(0.03 * np.cos(2 * np.pi * j / h), 0.02 * np.sin(2 * np.pi * i / w))
     sx, sy, tx, ty = render(w, h, d, zX, tX, zY, tY)
     P = O.OracleProblem(sx, sy, tx, ty, alpha=0.01)
     prm, stats = P.prealign_full(2, max_iter=300)
@@ -103,5 +130,5 @@ def test_recovers_known_offsets_and_tilts():
     rel = (aX[:, None] + gX[:, None] * (i[None, :] - 0.5 * (w - 1))) - (aY[None, :] + gY[None, :] * (j[:, None] - 0.5 * (h - 1)))
     true = (zX[:, None] + tX[:, None] * (i[None, :] - 0.5 * (w - 1))) - (zY[None, :] + tY[None, :] * (j[:, None] - 0.5 * (h - 1)))
     err = np.sqrt(np.mean((rel - true) ** 2))
-    assert err < 0.05, err
-    assert np.abs(gX - tX).max() < 0.01 and np.abs(gY - tY).max() < 0.01
+    assert err < 0.02, err
+    assert np.abs(gX - tX).max() < 0.002 and np.abs(gY - tY).max() < 0.002
