@@ -345,6 +345,17 @@ def run_ours(args):
                  "evals": int(sum(s["evals"] for s in stats)), "iters": [s["iters"] for s in stats],
                  "status": [s["status"] for s in stats]}
 
+    # ---- rough axial prealignment of the pair (stage 1: per-B-scan offsets and tilts, all levels)
+    prealign = None
+    if not args.no_solve:
+        barrier()
+        t0 = time.perf_counter()
+        _, _, pst = P.prealign_full(want_disp=False)
+        torch.cuda.synchronize()
+        prealign = {"seconds_per_pair": time.perf_counter() - t0, "levels": levels,
+                    "evals": int(sum(s["evals"] for s in pst)), "iters": [s["iters"] for s in pst],
+                    "status": [s["status"] for s in pst]}
+
     # ---- final resampling + merging of the pair (level 0, at the solution or the true field)
     Dm = out if solve is not None else D
     mo = P.merge(Dm, outputs=("merged", "weights", "angio"))
@@ -406,6 +417,7 @@ def run_ours(args):
         "gpu_launches": 3 * args.steps,
         "clocks": clk,
         "solve": solve,
+        "prealign": prealign,
         "merge": merge,
         "enface": enf,
     }
