@@ -240,6 +240,10 @@ struct octmc_lbfgs {
     return rejected;
   }
 
+  // Drops a launched prepare whose results are not wanted (the history is
+  // untouched until finish_prepare).
+  void cancel_prepare() { pend_new = pend_g = false; }
+
   int prepare(const double* g, bool new_pair) {
     launch_prepare(g, new_pair);
     CK(cudaStreamSynchronize(st));
@@ -681,6 +685,7 @@ struct SolveMachine {
   int rc = OCTMC_OK;
   bool dots_pending = false;
   int dots_kind = 0;  // 1: direction after reset/start, 2: after an accepted step
+  bool spec = false;  // the pair and dot products of the current trial are in flight
   double *x, *g, *xt, *gt, *xb, *gb, *dir;
   double f = 0, dg0 = 0, a = 0, lo = 0, hi = 0, fb = 0, ft = 0, eta = 1.0;
   bool have_lo = false;
@@ -714,6 +719,7 @@ struct SolveMachine {
     iters = evals = small = retried = 0;
     status = 1;
     dots_pending = false;
+    spec = false;
     eta = 1.0;
     ph = P->have_ang ? ETA : INIT;
   }
@@ -728,6 +734,20 @@ struct SolveMachine {
     P->opt->launch_prepare(gv, new_pair);
     dots_pending = true;
     dots_kind = kind;
+  }
+
+  // Called after the evaluation of a trial point has been enqueued and
+  // before the stream is synchronised: enqueues the history pair
+  // (xt - x, gt - g) and the dot products an accepted step needs, so that an
+  // accepted trial costs one synchronisation instead of two.  A rejected
+  // trial drops them (the pair buffer is the free one, the history is only
+  // changed by finish_prepare).
+  void speculate() {
+    if (ph != TRIAL) return;
+    octmc_lbfgs* O = P->opt;
+    CK(launch_sub2(xt, x, gt, g, O->S[O->spare], O->Y[O->spare], n(), P->st));
+    O->launch_prepare(gt, true);
+    spec = true;
   }
 
   void on_eval() {
@@ -762,6 +782,12 @@ struct SolveMachine {
     } else {
       accepted = true;
     }
+    bool had_spec = spec;
+    spec = false;
+    if (had_spec && !accepted) {
+      P->opt->cancel_prepare();
+      had_spec = false;
+    }
     if (!accepted && ls < P->desc.max_ls) {
       CK(launch_axpy(x, a, dir, xt, n(), P->st));
       return;
@@ -784,13 +810,18 @@ struct SolveMachine {
     }
     retried = 0;
     octmc_lbfgs* O = P->opt;
-    CK(launch_sub2(xt, x, gt, g, O->S[O->spare], O->Y[O->spare], n(), P->st));
+    if (!had_spec) CK(launch_sub2(xt, x, gt, g, O->S[O->spare], O->Y[O->spare], n(), P->st));
     const double rel = (f - ft) / std::max(std::max(std::fabs(f), std::fabs(ft)), 1.0);
     std::swap(x, xt);
     std::swap(g, gt);
     f = ft;
     iters++;
     small = (rel < P->desc.ftol) ? small + 1 : 0;
+    if (had_spec) {  // pair and dot products are already on the host
+      dots_kind = 2;
+      on_dots();
+      return;
+    }
     want_dots(g, true, 2);
   }
 
@@ -857,6 +888,7 @@ int run_machine(SolveMachine& M) {
   while (M.ph != SolveMachine::DONE) {
     std::vector<EvalReq> r{M.request()};
     eval_batch(M.P->st, r);
+    M.speculate();
     CK(cudaStreamSynchronize(M.P->st));
     collect_profiles(r);
     M.on_eval();
@@ -1126,6 +1158,7 @@ struct octmc_server {
     reqs.reserve(active.size());
     for (auto& r : active) reqs.push_back(r->M->request());
     eval_batch(st, reqs);
+    for (auto& r : active) r->M->speculate();
     CK(cudaStreamSynchronize(st));
     bool dots = false;
     for (auto& r : active) {

@@ -130,8 +130,11 @@ inline unsigned grid_for(int64_t n) {
 
 }  // namespace
 
+// At least kPerThread elements per thread: every block ends in float64
+// butterflies (slow on this GPU), so short vectors get few blocks.
+constexpr int kPerThread = 8;
 int dots_grid_blocks(int64_t n) {
-  int64_t b = (n + kThreads - 1) / kThreads;
+  int64_t b = (n + (int64_t)kThreads * kPerThread - 1) / ((int64_t)kThreads * kPerThread);
   if (b < 1) b = 1;
   if (b > kMaxDotBlocks) b = kMaxDotBlocks;
   return (int)b;
