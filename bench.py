@@ -99,6 +99,7 @@ def parse_args():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-octa", action="store_true", help="skip the en-face projection timing")
+    ap.add_argument("--no-storage", action="store_true", help="skip the 16-bit storage timing")
     ap.add_argument("--serve", action="store_true",
                     help="serving workload instead: Poisson arrivals of mixed-size BF16 pairs")
     ap.add_argument("--serve-requests", type=int, default=200)
@@ -283,7 +284,7 @@ def run_ours(args):
                       pair["vx"], pair["vy"], levels=levels)
     D = torch.from_numpy(np.ascontiguousarray(pair["truth"])).cuda()
     G = torch.empty_like(D)
-    P.compute_eta(0, D)
+    eta0 = P.compute_eta(0, D)
 
     def barrier():
         torch.cuda.synchronize()
@@ -373,6 +374,29 @@ def run_ours(args):
     merge = {"ms": merge_ms, "bytes": mb, "gbs": mb / merge_ms / 1e6, "outputs": list(mo),
              "note": "weights (density splat + gather) and resample-merge kernels, one host sync per call"}
 
+    # ---- the same evaluations with bfloat16 / float16 volume storage (float32 arithmetic)
+    storage = {}
+    if not args.no_storage:
+        for name, code in (("bf16", octmc.BF16), ("f16", octmc.F16)):
+            Q = octmc.Problem(pair["sx"], pair["sy"], pair["tx"], pair["ty"], pair["ax"], pair["ay"],
+                              pair["vx"], pair["vy"], levels=1, storage=code)
+            Q.set_eta(0, eta0)
+            for _ in range(5):
+                Q.eval_objective_grad(0, D, G)
+            Q.profile_enable(True)
+            barrier()
+            e0.record(stream)
+            for _ in range(args.steps):
+                Q.eval_objective_grad(0, D, G)
+            e1.record(stream)
+            barrier()
+            sms = e0.elapsed_time(e1)
+            km, kn = Q.profile_read()
+            storage[name] = {"evals_per_s": args.steps / (sms / 1e3), "data_kernel_ms": km / max(kn, 1),
+                             "volume_bytes": int(2 * w * h * ((d + 3) // 4 * 4) * 2)}
+            Q.destroy_problem()
+            del Q
+
     # ---- angiography preprocessing of one scan of the pair's size (Sec. 2.2, 2.3)
     enf = None
     if not args.no_octa:
@@ -417,6 +441,7 @@ def run_ours(args):
         "gpu_launches": 3 * args.steps,
         "clocks": clk,
         "solve": solve,
+        "storage_16bit": storage or None,
         "prealign": prealign,
         "merge": merge,
         "enface": enf,
