@@ -51,6 +51,13 @@ def test_host_only_calls(lib_path):
     assert L.octmc_create_problem(ctypes.byref(d), ctypes.byref(h)) == -1  # w = h = d = 0
     assert L.octmc_level_shape(None, 0, None, None, None) == -1
     assert L.octmc_lbfgs_create(0, 8, None, ctypes.byref(h)) == -1
+    # the adjacent steps validate their arguments before touching the device
+    assert L.octmc_merge(None, None, 2.0, 0.05, None, None, None, None, None) == -1
+    assert L.octmc_prealign_full(None, None, None, None) == -1
+    assert L.octmc_prealign_eval(None, 0, None, None, None) == -1
+    assert L.octmc_saccade_validity(None, 4, 4, 4, 0, None, None, None) == -1
+    assert L.octmc_saccade_validity(None, 4, 4, 4, 2, None, None, None) == -1
+    assert L.octmc_enface(None, None, 4, 4, 4, 0, None, 0.05, 0.95, 0.1, 0.0, None, None, None, None) == -1
 
 
 def test_product_path_has_no_fallback(monkeypatch, tmp_path):
