@@ -543,6 +543,25 @@ struct EvalReq {
   double delta0;
 };
 
+// A non-blocking side stream with its fork/join events, one per thread and
+// device (created on first use, kept for the life of the thread).
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+SideStream& side_stream() {
+  thread_local std::map<int, SideStream> per_device;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  SideStream& ss = per_device[dev];
+  if (!ss.s) {
+    CK(cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming));
+  }
+  return ss;
+}
+
 // Enqueues the evaluations of several problems as one batch: msum, data
 // (one launch per storage dtype) and reg kernels over all of them, then the
 // copy of every EvalResult to its problem's pinned host copy.  A problem
@@ -599,7 +618,13 @@ void eval_batch(cudaStream_t st, const std::vector<EvalReq>& reqs) {
       R.counter = P->counters + 1;
       RM.b0[k + 1] = RM.b0[k] + reg_grid_blocks(n);
     }
-    CK(launch_msum_multi(MM, st));
+    // The mean-term sums only feed the regulariser kernel: they run on a side
+    // stream, overlapped with the data kernel, and are joined before it.
+    SideStream& ss = side_stream();
+    CK(cudaEventRecord(ss.fork, st));
+    CK(cudaStreamWaitEvent(ss.s, ss.fork, 0));
+    CK(launch_msum_multi(MM, ss.s));
+    CK(cudaEventRecord(ss.join, ss.s));
     octmc_problem* P0 = reqs[c0].P;
     const bool prof = (ns == 1 && P0->profile);
     if (prof) CK(cudaEventRecord(P0->ev0, st));
@@ -612,6 +637,7 @@ void eval_batch(cudaStream_t st, const std::vector<EvalReq>& reqs) {
       CK(cudaEventRecord(P0->ev1, st));
       P0->prof_pending = true;
     }
+    CK(cudaStreamWaitEvent(st, ss.join, 0));
     CK(launch_reg_multi(RM, st));
     for (int k = 0; k < ns; k++) {
       octmc_problem* P = reqs[c0 + k].P;
