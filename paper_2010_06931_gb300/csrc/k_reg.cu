@@ -136,38 +136,41 @@ __device__ void reg_body(const RegArgs& A, int blk, int nblk) {
 #pragma unroll
   for (int c = 0; c < 3; c++) two_mu_s[c] = (float)(2.0 * A.mu * A.result->msum[c]);
   double v[4] = {0.0, 0.0, 0.0, 0.0};  // S^str, S^ang, R, grad . dir
-  for (int64_t p = (int64_t)blk * kThreads + threadIdx.x; p < n; p += (int64_t)nblk * kThreads) {
+  // one work item per A-scan and scan (2 n items): the three components of
+  // one volume's displacement; the A-scan's S^str, S^ang go with scan X
+  for (int64_t e = (int64_t)blk * kThreads + threadIdx.x; e < 2 * n; e += (int64_t)nblk * kThreads) {
+    const int V = e >= n ? 1 : 0;
+    const int64_t p = e - V * n;
     float r = 0.f, gd = 0.f;
+    const int nx = L.next[V][p], pv = L.prev[V][p];
+    const float wn = nx >= 0 ? L.wnext[V][p] : 0.f;
+    const float wp = pv >= 0 ? L.wprev[V][p] : 0.f;
 #pragma unroll
-    for (int V = 0; V < 2; V++) {
-      const int nx = L.next[V][p], pv = L.prev[V][p];
-      const float wn = nx >= 0 ? L.wnext[V][p] : 0.f;
-      const float wp = pv >= 0 ? L.wprev[V][p] : 0.f;
-#pragma unroll
-      for (int c = 0; c < 3; c++) {
-        const double* dc = A.disp + (V * 3 + c) * n;
-        const float x = narrow_trunc(dc[p]);
-        float gr = 0.f;
-        if (nx >= 0) {  // pair (p, next) is counted at its first sample
-          float dl;
-          r = fmaf(wn, huber(narrow_trunc(dc[nx]) - x, inv_eps, &dl), r);
-          gr = fmaf(-wn, dl, gr);
-        }
-        if (pv >= 0) {
-          float dl;
-          huber(x - narrow_trunc(dc[pv]), inv_eps, &dl);
-          gr = fmaf(wp, dl, gr);
-        }
-        if (A.grad) {
-          const int64_t gi = (V * 3 + c) * n + p;
-          const float g = A.gdata[gi] + fmaf(alpha, gr, two_mu_s[c]);
-          A.grad[gi] = widen_exact(g);
-          if (A.dir) gd = fmaf(g, narrow_trunc(A.dir[gi]), gd);
-        }
+    for (int c = 0; c < 3; c++) {
+      const double* dc = A.disp + (V * 3 + c) * n;
+      const float x = narrow_trunc(dc[p]);
+      float gr = 0.f;
+      if (nx >= 0) {  // pair (p, next) is counted at its first sample
+        float dl;
+        r = fmaf(wn, huber(narrow_trunc(dc[nx]) - x, inv_eps, &dl), r);
+        gr = fmaf(-wn, dl, gr);
+      }
+      if (pv >= 0) {
+        float dl;
+        huber(x - narrow_trunc(dc[pv]), inv_eps, &dl);
+        gr = fmaf(wp, dl, gr);
+      }
+      if (A.grad) {
+        const int64_t gi = (V * 3 + c) * n + p;
+        const float g = A.gdata[gi] + fmaf(alpha, gr, two_mu_s[c]);
+        A.grad[gi] = widen_exact(g);
+        if (A.dir) gd = fmaf(g, narrow_trunc(A.dir[gi]), gd);
       }
     }
-    v[0] += widen_exact(A.str_in[p]);
-    v[1] += widen_exact(A.ang_in[p]);
+    if (V == 0) {
+      v[0] += widen_exact(A.str_in[p]);
+      v[1] += widen_exact(A.ang_in[p]);
+    }
     v[2] += widen_exact(r);
     v[3] += widen_exact(gd);
   }
@@ -216,7 +219,7 @@ cudaError_t launch_reg_multi(const RegMulti& M, cudaStream_t s) {
 }
 
 int reg_grid_blocks(int64_t n) {
-  int64_t b = (n + kThreads - 1) / kThreads;
+  int64_t b = (2 * n + kThreads - 1) / kThreads;
   return (int)(b < 1 ? 1 : (b > kMaxRegBlocks ? kMaxRegBlocks : b));
 }
 
