@@ -177,15 +177,21 @@ __global__ void __launch_bounds__(kSx * kSy) median3_kernel(const float* __restr
   const int i = blockIdx.y * kSy + threadIdx.y;
   const int j = blockIdx.z;
   if (k >= d || i >= w) return;
+  // offsets of the clamped neighbours from the voxel, per axis
+  const int64_t row = (int64_t)w * d;
+  const float* c0 = in + (int64_t)j * row + (int64_t)i * d + k;
+  const int64_t ro[3] = {(int64_t)(clampn(j - 1, h) - j) * row, 0, (int64_t)(clampn(j + 1, h) - j) * row};
+  const int co[3] = {(clampn(i - 1, w) - i) * d, 0, (clampn(i + 1, w) - i) * d};
+  const int ko[3] = {k > 0 ? -1 : 0, 0, k + 1 < d ? 1 : 0};
   float v[27];
   int c = 0;
 #pragma unroll
-  for (int dj = -1; dj <= 1; dj++)
+  for (int dj = 0; dj < 3; dj++)
 #pragma unroll
-    for (int di = -1; di <= 1; di++) {
-      const float* col = in + ((int64_t)clampn(j + dj, h) * w + clampn(i + di, w)) * d;
+    for (int di = 0; di < 3; di++) {
+      const float* col = c0 + ro[dj] + co[di];
 #pragma unroll
-      for (int dk = -1; dk <= 1; dk++) v[c++] = __ldg(col + clampn(k + dk, d));
+      for (int dk = 0; dk < 3; dk++) v[c++] = __ldg(col + ko[dk]);
     }
   float a[15], rest[12];
 #pragma unroll
@@ -200,18 +206,20 @@ __global__ void __launch_bounds__(kSx * kSy) median3_kernel(const float* __restr
   out[((int64_t)j * w + i) * d + k] = fmaxf(fminf(x, y), fminf(fmaxf(x, y), z));
 }
 
+template <int AXIS>
 __global__ void __launch_bounds__(kSx * kSy) rank15_kernel(const float* __restrict__ in, int w, int h, int d,
-                                                           int axis, float* __restrict__ out) {
+                                                           float* __restrict__ out) {
   const int k = blockIdx.x * kSx + threadIdx.x;
   const int i = blockIdx.y * kSy + threadIdx.y;
   const int j = blockIdx.z;
   if (k >= d || i >= w) return;
+  const int64_t row = (int64_t)w * d;
+  const float* c0 = in + (int64_t)j * row + (int64_t)i * d + k;
   float a1 = INFINITY, a2 = INFINITY, a3 = INFINITY;
 #pragma unroll
   for (int o = -7; o <= 7; o++) {
-    const int ii = axis == 0 ? clampn(i + o, w) : i;
-    const int jj = axis == 1 ? clampn(j + o, h) : j;
-    const float x = __ldg(in + ((int64_t)jj * w + ii) * d + k);
+    const int64_t off = AXIS == 0 ? (int64_t)((clampn(i + o, w) - i) * d) : (int64_t)(clampn(j + o, h) - j) * row;
+    const float x = __ldg(c0 + off);
     const float t = fmaxf(a1, x);
     a1 = fminf(a1, x);
     const float u = fmaxf(a2, t);
@@ -551,9 +559,12 @@ extern "C" int octmc_enface(const float* octa, const float* oct, int w, int h, i
     const dim3 sb(kSx, kSy), sg((unsigned)((d + kSx - 1) / kSx), (unsigned)((w + kSy - 1) / kSy), (unsigned)h);
     median3_kernel<<<sg, sb, 0, st>>>(octa, w, h, d, m3);
     ck(cudaGetLastError());
-    rank15_kernel<<<sg, sb, 0, st>>>(m3, w, h, d, fast_axis, r1);
+    // fast axis first, then the slow axis
+    if (fast_axis == 0) rank15_kernel<0><<<sg, sb, 0, st>>>(m3, w, h, d, r1);
+    else rank15_kernel<1><<<sg, sb, 0, st>>>(m3, w, h, d, r1);
     ck(cudaGetLastError());
-    rank15_kernel<<<sg, sb, 0, st>>>(r1, w, h, d, 1 - fast_axis, r2);
+    if (fast_axis == 0) rank15_kernel<1><<<sg, sb, 0, st>>>(r1, w, h, d, r2);
+    else rank15_kernel<0><<<sg, sb, 0, st>>>(r1, w, h, d, r2);
     ck(cudaGetLastError());
     // percentiles of the filtered voxels of the valid B-scans
     for (int pass = 0; pass < 3; pass++) {
