@@ -23,7 +23,10 @@
  *  - Objective (Eq. 1 with Eq. 9): f = eta*S^str + S^ang/eta + alpha*R + M.
  *  - Every call is ordered on the problem's CUDA stream; "device" pointers
  *    are CUDA global memory the caller owns; "host" pointers are ordinary
- *    memory.  Calls on one problem are not thread-safe.
+ *    memory.  Calls on one problem are not thread-safe.  An evaluation forks
+ *    the mean-term sums onto an internal stream of the calling thread and
+ *    joins them back before its regulariser kernel, so the caller sees
+ *    plain stream order.
  *  - Return codes: 0 OK, 1 NOT_CONVERGED (soft: results are valid), negative
  *    = hard error (see OCTMC_ERR_*); no exception crosses this boundary.
  */
