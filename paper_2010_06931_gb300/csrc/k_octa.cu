@@ -7,9 +7,10 @@
 //                        the OCT threshold
 //   validity_kernel      mu, sigma of the B-scan means, the 3-sigma test and
 //                        the +-2 B-scan dilation (one block, float64)
-//   median3_kernel       3x3x3 median per voxel (edge replicated) by
-//                        forgetful selection: 15 candidates, repeatedly drop
-//                        the minimum and maximum and take in the next sample
+//   median3_kernel       3x3x3 median per voxel (edge replicated): the 9
+//                        depth triples sorted, 14 samples provably on either
+//                        side of the median dropped, forgetful selection of
+//                        the median of the 13 others
 //   rank15_kernel        3rd smallest of 15 samples along x or y (edge
 //                        replicated) with a 3-deep insertion network
 //   radix_hist_kernel /  exact order statistics of the filtered voxels of the
@@ -137,32 +138,78 @@ __global__ void __launch_bounds__(1024) validity_kernel(const double* __restrict
 // ---------------------------------------------------------------- filters
 __device__ __forceinline__ int clampn(int i, int n) { return i < 0 ? 0 : (i >= n ? n - 1 : i); }
 
-// a[lo] <- min of a[lo..14], a[14] <- max of a[lo..14] (others permuted).
-template <int LO>
-__device__ __forceinline__ void minmax_pass(float (&a)[15]) {
-  float mn = fminf(a[LO], a[14]), mx = fmaxf(a[LO], a[14]);
-  a[LO] = mn;
-  a[14] = mx;
+__device__ __forceinline__ void cmpx(float& a, float& b) {  // a <- min, b <- max
+  const float mn = fminf(a, b), mx = fmaxf(a, b);
+  a = mn;
+  b = mx;
+}
+
+// Forgetful selection of the median of N = W + M values: a[0..W-1] holds
+// the first W, rest[0..M-1] the others (W = (N+1)/2 + 1).  Each step moves
+// the minimum of the current window a[LO..W-1] to a[LO] and its maximum to
+// a[W-1], forgets both (the window start advances, the next value replaces
+// the maximum); three candidates remain and the median is their middle one.
+template <int W, int M, int LO = 0>
+__device__ __forceinline__ void forget_steps(float (&a)[W], const float (&rest)[M]) {
+  if constexpr (LO < M) {
+    cmpx(a[LO], a[W - 1]);
 #pragma unroll
-  for (int i = LO + 1; i < 14; i++) {
-    mn = fminf(a[LO], a[i]);
-    mx = fmaxf(a[LO], a[i]);
-    a[LO] = mn;
-    a[i] = mx;
-    mn = fminf(a[i], a[14]);
-    mx = fmaxf(a[i], a[14]);
-    a[i] = mn;
-    a[14] = mx;
+    for (int i = LO + 1; i < W - 1; i++) {
+      cmpx(a[LO], a[i]);
+      cmpx(a[i], a[W - 1]);
+    }
+    a[W - 1] = rest[LO];
+    forget_steps<W, M, LO + 1>(a, rest);
   }
 }
 
-template <int LO>
-__device__ __forceinline__ void forget_steps(float (&a)[15], const float (&rest)[12]) {
-  if constexpr (LO < 12) {
-    minmax_pass<LO>(a);
-    a[14] = rest[LO];  // the maximum is forgotten, the next sample takes its place
-    forget_steps<LO + 1>(a, rest);
+__device__ __forceinline__ float median3_of(float x, float y, float z) {
+  return fmaxf(fminf(x, y), fminf(fmaxf(x, y), z));
+}
+
+// The median of the 27 samples v[9][3] (9 neighbour columns, 3 depths):
+// sort each column's 3 samples into (low, mid, high); in the order of the
+// 27 values the 5 smallest lows and the 2 smallest mids lie at or below the
+// median (each has at least 14 values at or above it), the 5 largest highs
+// and the 2 largest mids at or above it, so the median is that of the 13
+// others -- the 4 largest lows, the middle 5 mids, the 4 smallest highs --
+// found by forgetful selection.  150 compare-exchanges instead of 192 for
+// forgetful selection over all 27.
+__device__ __forceinline__ float median27(float (&v)[9][3]) {
+  float lo[9], mid[9], hi[9];
+#pragma unroll
+  for (int c = 0; c < 9; c++) {
+    cmpx(v[c][0], v[c][1]);
+    cmpx(v[c][1], v[c][2]);
+    cmpx(v[c][0], v[c][1]);
+    lo[c] = v[c][0];
+    mid[c] = v[c][1];
+    hi[c] = v[c][2];
   }
+  // the 4 largest lows to lo[5..8]
+#pragma unroll
+  for (int e = 8; e >= 5; e--)
+#pragma unroll
+    for (int i = 0; i < e; i++) cmpx(lo[i], lo[e]);
+  // the 4 smallest highs to hi[0..3]
+#pragma unroll
+  for (int b = 0; b <= 3; b++)
+#pragma unroll
+    for (int i = b + 1; i < 9; i++) cmpx(hi[b], hi[i]);
+  // the 2 smallest mids to mid[0..1], the 2 largest to mid[7..8]
+#pragma unroll
+  for (int r = 0; r < 2; r++) {
+    cmpx(mid[r], mid[8 - r]);
+#pragma unroll
+    for (int i = r + 1; i < 8 - r; i++) {
+      cmpx(mid[r], mid[i]);
+      cmpx(mid[i], mid[8 - r]);
+    }
+  }
+  float a[8] = {lo[5], lo[6], lo[7], lo[8], mid[2], mid[3], mid[4], mid[5]};
+  const float rest[5] = {mid[6], hi[0], hi[1], hi[2], hi[3]};
+  forget_steps<8, 5>(a, rest);
+  return median3_of(a[5], a[6], a[7]);
 }
 
 // Stencil launch geometry: block (32 depths, 8 columns i), grid (depth
@@ -183,27 +230,16 @@ __global__ void __launch_bounds__(kSx * kSy) median3_kernel(const float* __restr
   const int64_t ro[3] = {(int64_t)(clampn(j - 1, h) - j) * row, 0, (int64_t)(clampn(j + 1, h) - j) * row};
   const int co[3] = {(clampn(i - 1, w) - i) * d, 0, (clampn(i + 1, w) - i) * d};
   const int ko[3] = {k > 0 ? -1 : 0, 0, k + 1 < d ? 1 : 0};
-  float v[27];
-  int c = 0;
+  float v[9][3];
 #pragma unroll
   for (int dj = 0; dj < 3; dj++)
 #pragma unroll
     for (int di = 0; di < 3; di++) {
       const float* col = c0 + ro[dj] + co[di];
 #pragma unroll
-      for (int dk = 0; dk < 3; dk++) v[c++] = __ldg(col + ko[dk]);
+      for (int dk = 0; dk < 3; dk++) v[dj * 3 + di][dk] = __ldg(col + ko[dk]);
     }
-  float a[15], rest[12];
-#pragma unroll
-  for (int t = 0; t < 15; t++) a[t] = v[t];
-#pragma unroll
-  for (int t = 0; t < 12; t++) rest[t] = v[15 + t];
-  // 12 steps: each drops the minimum (window start moves) and the maximum
-  // (replaced by the next sample); 3 candidates remain, the median is their
-  // middle value
-  forget_steps<0>(a, rest);
-  const float x = a[12], y = a[13], z = a[14];
-  out[((int64_t)j * w + i) * d + k] = fmaxf(fminf(x, y), fminf(fmaxf(x, y), z));
+  out[((int64_t)j * w + i) * d + k] = median27(v);
 }
 
 template <int AXIS>
@@ -281,9 +317,15 @@ __global__ void __launch_bounds__(kT) radix_hist_kernel(const float* __restrict_
       cur[t] = 0u;
       cnt[t] = 0u;
     }
+    // whether the current A-scan's B-scan is selected (recomputed when the
+    // run crosses into the next A-scan)
+    auto selected = [&](int64_t pp) {
+      const int b = fast_axis == 0 ? (int)(pp / w) : (int)(pp % w);
+      return !(any_valid && v[b] == 0.0f);
+    };
+    bool sel_p = selected(p);
     for (int q = 0; q < kRun && e < n; q++, e++) {
-      const int b = fast_axis == 0 ? (int)(p / w) : (int)(p % w);
-      if (!(any_valid && v[b] == 0.0f)) {
+      if (sel_p) {
         const unsigned key = order_key(vol[e]);
         const unsigned dig = (key >> sft) & msk;
         const unsigned hi = hs >= 32 ? 0u : (key >> hs);
@@ -301,6 +343,7 @@ __global__ void __launch_bounds__(kT) radix_hist_kernel(const float* __restrict_
       if (++k == d) {
         k = 0;
         p++;
+        if (q + 1 < kRun && e + 1 < n) sel_p = selected(p);
       }
     }
 #pragma unroll
