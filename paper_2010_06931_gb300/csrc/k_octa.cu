@@ -324,9 +324,27 @@ __global__ void __launch_bounds__(kT) radix_hist_kernel(const float* __restrict_
       return !(any_valid && v[b] == 0.0f);
     };
     bool sel_p = selected(p);
-    for (int q = 0; q < kRun && e < n; q++, e++) {
+    // the run's samples first (independent loads, 128-bit when the run is
+    // whole and aligned), then the counting
+    float x[kRun];
+    if (e + kRun <= n && ((reinterpret_cast<uintptr_t>(vol + e) & 15u) == 0)) {
+#pragma unroll
+      for (int c = 0; c < kRun / 4; c++) {
+        const float4 f = __ldg(reinterpret_cast<const float4*>(vol + e) + c);
+        x[4 * c] = f.x;
+        x[4 * c + 1] = f.y;
+        x[4 * c + 2] = f.z;
+        x[4 * c + 3] = f.w;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < kRun; q++) x[q] = e + q < n ? __ldg(vol + e + q) : 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < kRun; q++, e++) {
+      if (e >= n) break;
       if (sel_p) {
-        const unsigned key = order_key(vol[e]);
+        const unsigned key = order_key(x[q]);
         const unsigned dig = (key >> sft) & msk;
         const unsigned hi = hs >= 32 ? 0u : (key >> hs);
 #pragma unroll
