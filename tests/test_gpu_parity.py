@@ -79,9 +79,12 @@ def test_eval_c1_at_truth_and_oct_only(c1):
     compare_eval(q, T, delta0=0.0)
 
 
-@pytest.mark.parametrize("shape", [(29, 37, 245), (5, 3, 1), (1, 7, 6), (8, 1, 117), (13, 11, 4)])
+@pytest.mark.parametrize("shape", [(29, 37, 245), (5, 3, 1), (1, 7, 6), (8, 1, 117), (13, 11, 4),
+                                   (6, 5, 52), (7, 9, 168), (9, 7, 169)])
 def test_eval_ragged_shapes(shape):
-    # depth not a multiple of 4 nor of the 116-sample blocks, odd grids, degenerate axes
+    # depth not a multiple of 4 nor of the 116-sample blocks, odd grids, degenerate axes;
+    # last blocks of 52 outputs (the most the split mapping takes: d = 52, 116 + 52) and
+    # of 53 (the least a full block takes: d = 116 + 53)
     h, w, d = shape
     p = make_pair(w, h, d, n_layers=4, n_slabs=1, n_saccades=1, max_saccade=2.0, drift_sigma=0.05, seed=3)
     rng = np.random.default_rng(5)
