@@ -255,7 +255,11 @@ int octmc_level_data(const octmc_problem *p, int level, float *sx, float *sy, fl
 /* ---------------------------------------------------------------------
  * Stand-alone L-BFGS (Sec. 2.1) over n float64 device values: the compact
  * representation of the inverse Hessian with gamma = s'y / y'y of the latest
- * pair; pairs with s'y <= 1e-12 y'y are rejected.
+ * pair; pairs with s'y <= 1e-12 y'y are rejected.  The pairs are stored
+ * rounded to float32 and their products with y and g are float32 FMAs summed
+ * in float64 across warps and blocks (about 1e-8 relative on the direction
+ * for well-conditioned histories); g'g, max|g| and the -gamma g term of the
+ * direction are float64, so an empty history gives exactly -g.  m is 1..32.
  * --------------------------------------------------------------------- */
 typedef struct octmc_lbfgs octmc_lbfgs;
 

@@ -105,21 +105,21 @@ struct octmc_lbfgs {
   int64_t n = 0;
   int m = 0;
   cudaStream_t st = nullptr;
-  std::vector<double*> S, Y;  // m + 1 buffers each
+  std::vector<float*> S, Y;   // m + 1 buffers each (float32 pairs)
   std::vector<int> order;     // stored pairs, oldest first (buffer ids)
   int spare = 0;              // buffer receiving the next pair
   std::vector<double> SY, YY; // (m+1)^2, indexed by buffer ids
   double* partials = nullptr;
   unsigned* counter = nullptr;
   double* dots_dev = nullptr;
-  double* dots_host = nullptr; // pinned, kMaxDots + 1
+  double* dots_host = nullptr; // pinned, hist_dots_outputs(2 (m + 1))
   // results of the last prepare(): per stored buffer s.g and y.g, g.g, max|g|
   std::vector<double> sg, yg;
   double gg = 0.0, gmax = 0.0;
 
   ~octmc_lbfgs() {
-    for (double* p : S) dfree(p);
-    for (double* p : Y) dfree(p);
+    for (float* p : S) dfree(p);
+    for (float* p : Y) dfree(p);
     dfree(partials);
     dfree(counter);
     dfree(dots_dev);
@@ -133,18 +133,19 @@ struct octmc_lbfgs {
     S.assign(m + 1, nullptr);
     Y.assign(m + 1, nullptr);
     for (int b = 0; b <= m; b++) {
-      S[b] = dalloc<double>((size_t)n);
-      Y[b] = dalloc<double>((size_t)n);
+      S[b] = dalloc<float>((size_t)n);
+      Y[b] = dalloc<float>((size_t)n);
     }
     SY.assign((size_t)(m + 1) * (m + 1), 0.0);
     YY.assign((size_t)(m + 1) * (m + 1), 0.0);
     sg.assign(m + 1, 0.0);
     yg.assign(m + 1, 0.0);
-    partials = dalloc<double>((size_t)(kMaxDots + 1) * dots_grid_blocks(n));
+    const int nout = hist_dots_outputs(2 * (m + 1));
+    partials = dalloc<double>((size_t)nout * hist_dots_blocks(n));
     counter = dalloc<unsigned>(1);
     CK(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
-    dots_dev = dalloc<double>(kMaxDots + 1);
-    CK(cudaMallocHost(&dots_host, sizeof(double) * (kMaxDots + 1)));
+    dots_dev = dalloc<double>(nout);
+    CK(cudaMallocHost(&dots_host, sizeof(double) * nout));
     reset();
   }
 
@@ -166,56 +167,47 @@ struct octmc_lbfgs {
   // tested (s'y > 1e-12 y'y) and appended (dropping the oldest when full);
   // if g != null, s.g and y.g for every stored pair plus g.g and max|g| are
   // taken for the next direction.  launch_prepare enqueues the dot products
-  // and their copy to pinned host memory; finish_prepare (after the stream
-  // has synchronised) updates the history.  It returns 1 if a new pair was
+  // (the stored pairs and the new one against the probes y_new and g) and
+  // their copy to pinned host memory; finish_prepare (after the stream has
+  // synchronised) updates the history.  It returns 1 if a new pair was
   // rejected.
   bool pend_new = false, pend_g = false;
-  int pend_first_g = 0;
-  std::vector<int> pend_cand;
+  int pend_K = 0;
+  std::vector<int> pend_cand;  // buffers of the history vectors, in order
 
   void launch_prepare(const double* g, bool new_pair) {
-    DotList dl;
-    dl.n = 0;
+    HistDots hd{};
+    int K = 0;
     const int nb = spare;
-    auto add = [&](const double* a, const double* b) {
-      dl.a[dl.n] = a;
-      dl.b[dl.n] = b;
-      dl.n++;
-    };
-    if (new_pair) {
-      add(S[nb], Y[nb]);
-      add(Y[nb], Y[nb]);
-      for (int b : order) {
-        add(S[b], Y[nb]);
-        add(Y[b], Y[nb]);
-      }
-    }
-    pend_first_g = dl.n;
     pend_cand = order;
     if (new_pair) pend_cand.push_back(nb);
-    if (g) {
-      for (int b : pend_cand) {
-        add(S[b], g);
-        add(Y[b], g);
-      }
-      add(g, g);
+    for (int b : pend_cand) {
+      hd.h[K++] = S[b];
+      hd.h[K++] = Y[b];
     }
+    hd.K = K;
+    hd.q0 = new_pair ? Y[nb] : nullptr;
+    hd.q1 = g;
+    pend_K = K;
     pend_new = new_pair;
     pend_g = (g != nullptr);
-    CK(launch_dots(dl, n, g, partials, counter, dots_dev, st));
-    CK(cudaMemcpyAsync(dots_host, dots_dev, sizeof(double) * (kMaxDots + 1), cudaMemcpyDeviceToHost, st));
+    CK(launch_hist_dots(hd, n, partials, counter, dots_dev, st));
+    CK(cudaMemcpyAsync(dots_host, dots_dev, sizeof(double) * hist_dots_outputs(K), cudaMemcpyDeviceToHost, st));
   }
 
+  // Output layout of hist_dots for history vector 2t (S of pend_cand[t]) and
+  // 2t+1 (Y of pend_cand[t]): [2v] = v . y_new, [2v+1] = v . g.
   int finish_prepare() {
     const double* r = dots_host;
-    const int nb = spare;
+    const int nb = spare, K = pend_K;
+    const int t_new = (int)order.size();  // the new pair's slot in pend_cand
     int rejected = 0;
     if (pend_new) {
-      const double s_y = r[0], y_y = r[1];
+      const double s_y = r[2 * (2 * t_new)], y_y = r[2 * K];
       if (s_y > 1e-12 * y_y && std::isfinite(s_y) && std::isfinite(y_y)) {
         for (size_t t = 0; t < order.size(); t++) {
-          sy(order[t], nb) = r[2 + 2 * t];
-          const double v = r[3 + 2 * t];
+          sy(order[t], nb) = r[2 * (2 * t)];
+          const double v = r[2 * (2 * t + 1)];
           yy(order[t], nb) = v;
           yy(nb, order[t]) = v;
         }
@@ -230,11 +222,11 @@ struct octmc_lbfgs {
     }
     if (pend_g) {
       for (size_t t = 0; t < pend_cand.size(); t++) {
-        sg[pend_cand[t]] = r[pend_first_g + 2 * t];
-        yg[pend_cand[t]] = r[pend_first_g + 2 * t + 1];
+        sg[pend_cand[t]] = r[2 * (2 * t) + 1];
+        yg[pend_cand[t]] = r[2 * (2 * t + 1) + 1];
       }
-      gg = r[pend_first_g + 2 * pend_cand.size()];
-      gmax = r[kMaxDots];
+      gg = r[2 * K + 1];
+      gmax = r[2 * K + 2];
     }
     pend_new = pend_g = false;
     return rejected;
@@ -255,7 +247,7 @@ struct octmc_lbfgs {
   // is not negative the history is dropped and dir = -g.
   double direction(const double* g, double* dir) {
     const int k = this->k();
-    LinComb lc;
+    HistComb lc{};
     double gd;
     if (k > 0) {
       const int last = order[k - 1];
@@ -283,30 +275,30 @@ struct octmc_lbfgs {
         for (int j = 0; j < i; j++) s -= sy(order[j], order[i]) * top[j];
         top[i] = s / sy(order[i], order[i]);
       }
-      lc.n = 0;
-      lc.v[lc.n] = g;
-      lc.c[lc.n++] = -gamma;
+      lc.g = g;
+      lc.cg = -gamma;
+      lc.K = 0;
       gd = -gamma * gg;
       for (int i = 0; i < k; i++) {
-        lc.v[lc.n] = S[order[i]];
-        lc.c[lc.n++] = -top[i];
-        lc.v[lc.n] = Y[order[i]];
-        lc.c[lc.n++] = gamma * u[i];
+        lc.h[lc.K] = S[order[i]];
+        lc.c[lc.K++] = (float)-top[i];
+        lc.h[lc.K] = Y[order[i]];
+        lc.c[lc.K++] = (float)(gamma * u[i]);
         gd += -top[i] * a[i] + gamma * u[i] * b[i];
       }
       if (!(gd < 0.0)) k_reset_steepest(lc, g, gd);
     } else {
       k_reset_steepest(lc, g, gd);
     }
-    CK(launch_lincomb(lc, n, dir, st));
+    CK(launch_hist_comb(lc, n, dir, st));
     return gd;
   }
 
-  void k_reset_steepest(LinComb& lc, const double* g, double& gd) {
+  void k_reset_steepest(HistComb& lc, const double* g, double& gd) {
     reset();
-    lc.n = 1;
-    lc.v[0] = g;
-    lc.c[0] = -1.0;
+    lc.g = g;
+    lc.cg = -1.0;
+    lc.K = 0;
     gd = -gg;
   }
 };
@@ -1105,7 +1097,7 @@ int64_t estimate_bytes_impl(const octmc_desc& D) {
   }
   const int64_t m = std::max(D.lbfgs_m, 1);
   total += n0 * (4 + 4 + 24);                       // per-A-scan partials, float gradient
-  total += (7 + 2 * (m + 1) + 1) * 6 * n0 * 8;      // solver vectors, history, result
+  total += (7 + 1) * 6 * n0 * 8 + 2 * (m + 1) * 6 * n0 * 4;  // solver vectors, result, float history
   total += 64 << 10;                                // small buffers
   return total + peak_tmp;
 }
@@ -1457,8 +1449,8 @@ void octmc_lbfgs_destroy(octmc_lbfgs* h) {
 int octmc_lbfgs_push(octmc_lbfgs* h, const double* s, const double* y) {
   if (!h || !s || !y) return OCTMC_ERR_INVALID_ARG;
   return guarded([&] {
-    CK(cudaMemcpyAsync(h->S[h->spare], s, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->st));
-    CK(cudaMemcpyAsync(h->Y[h->spare], y, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->st));
+    CK(launch_to_f32(s, h->S[h->spare], h->n, h->st));
+    CK(launch_to_f32(y, h->Y[h->spare], h->n, h->st));
     return h->prepare(nullptr, true);
   });
 }

@@ -269,25 +269,39 @@ cudaError_t launch_unpad_depth(const void* vol, int dtype, int64_t columns, int 
                                cudaStream_t s);
 cudaError_t launch_convert(const float* in, void* out, int dtype, int64_t n, cudaStream_t s);
 
-// L-BFGS vector kernels (float64).
-constexpr int kMaxDots = 80;
-constexpr int kMaxVecs = 72;
-struct DotList {
-  const double* a[kMaxDots];
-  const double* b[kMaxDots];
-  int n;
+// L-BFGS vector kernels.  The iterate x, the gradient g and the direction
+// are float64; the history pairs (s, y) are stored in float32 (each formed
+// as a float64 difference, then rounded).  Products with the history are
+// taken in float32 (float64 runs at 1/64 of the float rate on this GPU) and
+// reduced across warps and blocks in float64 with fixed trees.
+constexpr int kMaxHist = 66;  // 2 (m + 1) history vectors for m <= 32
+// Dot products of K history vectors with up to two probes: q0 (float32,
+// the newest y) and q1 (float64, a gradient); a null probe reads as 0.
+// Outputs: [2k] = h_k . q0, [2k+1] = h_k . q1 (k < K), [2K] = q0 . q0,
+// [2K+1] = q1 . q1 (float64 products), [2K+2] = max |q1| (exact).
+struct HistDots {
+  const float* h[kMaxHist];
+  int K;
+  const float* q0;
+  const double* q1;
 };
-struct LinComb {
-  const double* v[kMaxVecs];
-  double c[kMaxVecs];
-  int n;
+__host__ __device__ inline int hist_dots_outputs(int K) { return 2 * K + 3; }
+// out = cg g + sum_k c_k h_k (the g term in float64, the history sum in float32).
+struct HistComb {
+  const double* g;
+  double cg;
+  const float* h[kMaxHist];
+  float c[kMaxHist];
+  int K;
 };
-int dots_grid_blocks(int64_t n);
-cudaError_t launch_dots(const DotList& dl, int64_t n, const double* maxabs_of, double* partials,
-                        unsigned* counter, double* out, cudaStream_t s);
-cudaError_t launch_lincomb(const LinComb& lc, int64_t n, double* out, cudaStream_t s);
+int hist_dots_blocks(int64_t n);
+cudaError_t launch_hist_dots(const HistDots& hd, int64_t n, double* partials, unsigned* counter, double* out,
+                             cudaStream_t s);
+cudaError_t launch_hist_comb(const HistComb& hc, int64_t n, double* out, cudaStream_t s);
+// s = x1 - x0, y = g1 - g0 (float64 differences rounded to float32).
 cudaError_t launch_sub2(const double* x1, const double* x0, const double* g1, const double* g0,
-                        double* s_out, double* y_out, int64_t n, cudaStream_t st);
+                        float* s_out, float* y_out, int64_t n, cudaStream_t st);
+cudaError_t launch_to_f32(const double* in, float* out, int64_t n, cudaStream_t s);
 cudaError_t launch_axpy(const double* x, double a, const double* d, double* out, int64_t n,
                         cudaStream_t s);
 

@@ -1,14 +1,22 @@
-// Float64 vector kernels of the on-device L-BFGS (Ploner et al. Sec. 2.1:
-// "gradient-based L-BFGS solver"): batched dot products with a fixed
-// reduction order, linear combinations, differences and axpy.
+// Vector kernels of the on-device L-BFGS (Ploner et al. Sec. 2.1:
+// "gradient-based L-BFGS solver"): dot products of the history with probe
+// vectors, the direction as a linear combination, pair differences and axpy.
+//
+// The history pairs are float32.  Double arithmetic runs at 1/64 of the
+// float rate on this GPU, so the products with the history are float32
+// FMAs; each thread sums at most a few elements, a warp sums its lanes
+// with a fixed float32 butterfly, and everything above the warp (warps of a
+// block, blocks of the grid) is float64 with fixed trees: deterministic.
 #include "common.cuh"
 
 namespace octmc {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kChunk = 8;          // dot products per block row
-constexpr int kMaxDotBlocks = 304; // blocks per chunk (2 per SM)
+constexpr int kWarps = kThreads / 32;
+constexpr int kHistChunk = 20;         // history vectors per block row
+constexpr int kPerThread = 8;          // elements per thread (at least)
+constexpr int kMaxDotBlocks = 8 * 152; // blocks per row
 
 __device__ bool last_block_2d(unsigned* counter) {
   __shared__ bool is_last;
@@ -23,95 +31,147 @@ __device__ bool last_block_2d(unsigned* counter) {
   return is_last;
 }
 
-// grid (G, chunks): block (bx, c) accumulates dots c*8 .. c*8+7 over a
-// strided share of the n elements; chunk 0 also takes max|maxabs_of|.
-// partials layout: [dot][G] and [kMaxDots][G] for the max.
-__global__ void __launch_bounds__(kThreads) dots_kernel(const DotList L, int64_t n,
-                                                        const double* __restrict__ maxabs_of,
-                                                        double* partials, unsigned* counter,
-                                                        double* out) {
-  __shared__ double sm[(kChunk + 1) * (kThreads / 32)];
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+
+// grid (G, rows): block (bx, r) takes history vectors r*20 .. r*20+19 over
+// a strided share of the n elements; row 0 also takes q0.q0, q1.q1 and
+// max|q1| (the maximum on the bit patterns: exact, and NaN wins).
+// partials layout: [output][G].
+__global__ void __launch_bounds__(kThreads) hist_dots_kernel(const HistDots D, int64_t n, double* partials,
+                                                             unsigned* counter, double* out) {
+  __shared__ double sm[(2 * kHistChunk + 3) * kWarps];
   const int G = gridDim.x;
-  const int c0 = blockIdx.y * kChunk;
-  double acc[kChunk + 1];
+  const int k0 = blockIdx.y * kHistChunk;
+  const int kn = min(kHistChunk, D.K - k0);  // <= 0 only in row 0 of an empty history
+  const bool first = blockIdx.y == 0;
+  const float* h[kHistChunk];
 #pragma unroll
-  for (int t = 0; t <= kChunk; t++) acc[t] = 0.0;
-  const double* a[kChunk];
-  const double* b[kChunk];
+  for (int k = 0; k < kHistChunk; k++) h[k] = (k < kn) ? D.h[k0 + k] : nullptr;
+  float a0[kHistChunk], a1[kHistChunk];
 #pragma unroll
-  for (int t = 0; t < kChunk; t++) {
-    a[t] = (c0 + t < L.n) ? L.a[c0 + t] : nullptr;
-    b[t] = (c0 + t < L.n) ? L.b[c0 + t] : nullptr;
-  }
-  const bool do_max = (blockIdx.y == 0) && maxabs_of;
+  for (int k = 0; k < kHistChunk; k++) a0[k] = a1[k] = 0.f;
+  float qq0 = 0.f;
+  double qq1 = 0.0;
+  unsigned long long mx = 0ull;
   for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < n; e += (int64_t)G * kThreads) {
+    const float v0 = D.q0 ? D.q0[e] : 0.f;
+    const double g = D.q1 ? D.q1[e] : 0.0;
+    const float v1 = (float)g;
 #pragma unroll
-    for (int t = 0; t < kChunk; t++)
-      if (a[t]) acc[t] = fma(a[t][e], b[t][e], acc[t]);
-    if (do_max) acc[kChunk] = fmax(acc[kChunk], fabs(maxabs_of[e]));
+    for (int k = 0; k < kHistChunk; k++) {
+      if (k < kn) {
+        const float hv = h[k][e];
+        a0[k] = fmaf(hv, v0, a0[k]);
+        a1[k] = fmaf(hv, v1, a1[k]);
+      }
+    }
+    if (first) {
+      qq0 = fmaf(v0, v0, qq0);
+      qq1 = fma(g, g, qq1);
+      mx = max(mx, abs_bits(g));
+    }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int t = 0; t <= kChunk; t++) {
-    double v = acc[t];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double u = __shfl_xor_sync(0xffffffffu, v, o);
-      v = (t == kChunk) ? fmax(v, u) : v + u;
-    }
-    if (lane == 0) sm[t * (kThreads / 32) + warp] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x <= kChunk) {
-    const int t = threadIdx.x;
-    double v = 0.0;
-    for (int w = 0; w < kThreads / 32; w++) {
-      const double u = sm[t * (kThreads / 32) + w];
-      v = (t == kChunk) ? fmax(v, u) : v + u;
-    }
-    if (t < kChunk && c0 + t < L.n) partials[(int64_t)(c0 + t) * G + blockIdx.x] = v;
-    if (t == kChunk && blockIdx.y == 0) partials[(int64_t)kMaxDots * G + blockIdx.x] = v;
-  }
-  if (last_block_2d(counter)) {
-    // the last block adds the partials of each dot: one warp per dot, lanes
-    // take a fixed strided share of the blocks, then a butterfly
-    for (int dd = warp; dd <= L.n; dd += kThreads / 32) {
-      const bool is_max = (dd == L.n);
-      const int64_t row = is_max ? kMaxDots : dd;
-      double v = 0.0;
-      for (int bx = lane; bx < G; bx += 32) {
-        const double u = partials[row * G + bx];
-        v = is_max ? fmax(v, u) : v + u;
-      }
+  for (int k = 0; k < kHistChunk; k++) {
+    if (k < kn) {
+      float u0 = a0[k], u1 = a1[k];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        const double u = __shfl_xor_sync(0xffffffffu, v, o);
-        v = is_max ? fmax(v, u) : v + u;
+        u0 += __shfl_xor_sync(0xffffffffu, u0, o);
+        u1 += __shfl_xor_sync(0xffffffffu, u1, o);
       }
-      if (lane == 0) out[is_max ? kMaxDots : dd] = v;
+      if (lane == 0) {
+        sm[(2 * k) * kWarps + warp] = u0;
+        sm[(2 * k + 1) * kWarps + warp] = u1;
+      }
+    }
+  }
+  if (first) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      qq0 += __shfl_xor_sync(0xffffffffu, qq0, o);
+      qq1 += __shfl_xor_sync(0xffffffffu, qq1, o);
+      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if (lane == 0) {
+      sm[(2 * kHistChunk) * kWarps + warp] = qq0;
+      sm[(2 * kHistChunk + 1) * kWarps + warp] = qq1;
+      sm[(2 * kHistChunk + 2) * kWarps + warp] = __longlong_as_double((long long)mx);
+    }
+  }
+  __syncthreads();
+  const int nloc = 2 * max(kn, 0);
+  for (int t = threadIdx.x; t < 2 * kHistChunk + 3; t += kThreads) {
+    if (t < nloc) {
+      double v = 0.0;
+      for (int w = 0; w < kWarps; w++) v += sm[t * kWarps + w];
+      partials[(int64_t)(2 * k0 + t) * G + blockIdx.x] = v;
+    } else if (first && t >= 2 * kHistChunk) {
+      const int x = t - 2 * kHistChunk;  // 0: q0.q0, 1: q1.q1, 2: max|q1|
+      double v = 0.0;
+      unsigned long long m = 0ull;
+      for (int w = 0; w < kWarps; w++) {
+        const double u = sm[t * kWarps + w];
+        if (x == 2) m = max(m, (unsigned long long)__double_as_longlong(u));
+        else v += u;
+      }
+      partials[(int64_t)(2 * D.K + x) * G + blockIdx.x] = (x == 2) ? __longlong_as_double((long long)m) : v;
+    }
+  }
+  if (last_block_2d(counter)) {
+    // one warp per output: lanes take a fixed strided share of the blocks,
+    // then a butterfly
+    const int nout = hist_dots_outputs(D.K);
+    for (int o = warp; o < nout; o += kWarps) {
+      const bool is_max = (o == nout - 1);
+      double v = 0.0;
+      unsigned long long m = 0ull;
+      for (int bx = lane; bx < G; bx += 32) {
+        const double u = partials[(int64_t)o * G + bx];
+        if (is_max) m = max(m, (unsigned long long)__double_as_longlong(u));
+        else v += u;
+      }
+#pragma unroll
+      for (int s = 16; s > 0; s >>= 1) {
+        v += __shfl_xor_sync(0xffffffffu, v, s);
+        m = max(m, __shfl_xor_sync(0xffffffffu, m, s));
+      }
+      if (lane == 0) out[o] = is_max ? __longlong_as_double((long long)m) : v;
     }
     __syncthreads();
     if (threadIdx.x == 0) *counter = 0u;
   }
 }
 
-__global__ void lincomb_kernel(const LinComb C, int64_t n, double* __restrict__ out) {
+// out = cg g + sum_k c_k h_k: the history sum in float32 (fixed order),
+// the g term and the final add in float64.
+__global__ void __launch_bounds__(kThreads) hist_comb_kernel(const HistComb C, int64_t n, double* __restrict__ out) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int v = 0; v < C.n; v++) s = fma(C.c[v], C.v[v][e], s);
-    out[e] = s;
+    float s = 0.f;
+#pragma unroll 8
+    for (int k = 0; k < C.K; k++) s = fmaf(C.c[k], C.h[k][e], s);
+    out[e] = fma(C.cg, C.g[e], (double)s);
   }
 }
 
 __global__ void sub2_kernel(const double* __restrict__ x1, const double* __restrict__ x0,
                             const double* __restrict__ g1, const double* __restrict__ g0,
-                            double* __restrict__ s, double* __restrict__ y, int64_t n) {
+                            float* __restrict__ s, float* __restrict__ y, int64_t n) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
-    s[e] = x1[e] - x0[e];
-    y[e] = g1[e] - g0[e];
+    s[e] = (float)(x1[e] - x0[e]);
+    y[e] = (float)(g1[e] - g0[e]);
   }
+}
+
+__global__ void to_f32_kernel(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = (float)in[e];
 }
 
 __global__ void axpy_kernel(const double* __restrict__ x, double a, const double* __restrict__ d,
@@ -130,32 +190,39 @@ inline unsigned grid_for(int64_t n) {
 
 }  // namespace
 
-// At least kPerThread elements per thread: every block ends in float64
-// butterflies (slow on this GPU), so short vectors get few blocks.
-constexpr int kPerThread = 8;
-int dots_grid_blocks(int64_t n) {
+// At least kPerThread elements per thread: each thread's float32 sums
+// stay short and every block ends in butterflies, so short vectors get few
+// blocks.
+int hist_dots_blocks(int64_t n) {
   int64_t b = (n + (int64_t)kThreads * kPerThread - 1) / ((int64_t)kThreads * kPerThread);
   if (b < 1) b = 1;
   if (b > kMaxDotBlocks) b = kMaxDotBlocks;
   return (int)b;
 }
 
-cudaError_t launch_dots(const DotList& dl, int64_t n, const double* maxabs_of, double* partials,
-                        unsigned* counter, double* out, cudaStream_t s) {
-  const int G = dots_grid_blocks(n);
-  const int chunks = dl.n > 0 ? (dl.n + kChunk - 1) / kChunk : 1;
-  dots_kernel<<<dim3(G, chunks), kThreads, 0, s>>>(dl, n, maxabs_of, partials, counter, out);
+cudaError_t launch_hist_dots(const HistDots& hd, int64_t n, double* partials, unsigned* counter, double* out,
+                             cudaStream_t s) {
+  if (hd.K < 0 || hd.K > kMaxHist) return cudaErrorInvalidValue;
+  const int G = hist_dots_blocks(n);
+  const int rows = hd.K > 0 ? (hd.K + kHistChunk - 1) / kHistChunk : 1;
+  hist_dots_kernel<<<dim3(G, rows), kThreads, 0, s>>>(hd, n, partials, counter, out);
   return cudaGetLastError();
 }
 
-cudaError_t launch_lincomb(const LinComb& lc, int64_t n, double* out, cudaStream_t s) {
-  lincomb_kernel<<<grid_for(n), kThreads, 0, s>>>(lc, n, out);
+cudaError_t launch_hist_comb(const HistComb& hc, int64_t n, double* out, cudaStream_t s) {
+  if (hc.K < 0 || hc.K > kMaxHist) return cudaErrorInvalidValue;
+  hist_comb_kernel<<<grid_for(n), kThreads, 0, s>>>(hc, n, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sub2(const double* x1, const double* x0, const double* g1, const double* g0,
-                        double* s_out, double* y_out, int64_t n, cudaStream_t st) {
+                        float* s_out, float* y_out, int64_t n, cudaStream_t st) {
   sub2_kernel<<<grid_for(n), kThreads, 0, st>>>(x1, x0, g1, g0, s_out, y_out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_f32(const double* in, float* out, int64_t n, cudaStream_t st) {
+  to_f32_kernel<<<grid_for(n), kThreads, 0, st>>>(in, out, n);
   return cudaGetLastError();
 }
 

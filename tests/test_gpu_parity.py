@@ -182,8 +182,15 @@ def test_lbfgs_direction_parity():
         assert H.push(cuda(s), cuda(y)) == 0
     d, gtd = H.direction(cuda(g))
     ref = O.lbfgs_direction(S[-8:], Y[-8:], g)  # the last 8 pairs are kept
-    assert rel_l2(d.cpu().numpy(), ref) < 1e-10
-    assert gtd == pytest.approx(float(g @ ref), rel=1e-10)
+    # The library keeps the pairs in float32 (relative rounding 2^-24; it moves this
+    # direction by 3e-9) and takes their products with y and g as float32 FMAs over
+    # <= 8 elements per thread and a 32-lane float32 butterfly before float64 sums:
+    # up to ~1e-6 relative error on a product with heavy cancellation, entering
+    # the direction only through the small history correction.
+    err = rel_l2(d.cpu().numpy(), ref)
+    print("lbfgs direction rel L2 %.3e, g'dir rel %.3e" % (err, abs(gtd - g @ ref) / abs(g @ ref)))
+    assert err < 1e-5
+    assert gtd == pytest.approx(float(g @ ref), rel=1e-5)
     # a pair with negative curvature is rejected and changes nothing
     assert H.push(cuda(S[0]), cuda(-Y[0])) == 1
     d2, _ = H.direction(cuda(g))
@@ -191,6 +198,37 @@ def test_lbfgs_direction_parity():
     H.reset()
     d3, gtd3 = H.direction(cuda(g))
     assert np.array_equal(d3.cpu().numpy(), -g) and gtd3 == pytest.approx(-(g @ g), rel=1e-12)
+
+
+def test_lbfgs_direction_parity_longest_history():
+    # m = 32 (the largest history a problem accepts): 66 history vectors, several
+    # block rows of the dot-product kernel, a ragged length
+    import paper_2010_06931_gb300 as octmc
+    rng = np.random.default_rng(7)
+    n = 3001
+    A = rng.uniform(0.5, 3.0, size=n)
+    S = [rng.normal(size=n) for _ in range(40)]
+    Y = [A * s + 0.01 * rng.normal(size=n) for s in S]
+    g = rng.normal(size=n)
+    H = octmc.Lbfgs(n, m=32)
+    for s, y in zip(S, Y):
+        assert H.push(cuda(s), cuda(y)) == 0
+    d, gtd = H.direction(cuda(g))
+    ref = O.lbfgs_direction(S[-32:], Y[-32:], g)
+    assert rel_l2(d.cpu().numpy(), ref) < 1e-5
+    assert gtd == pytest.approx(float(g @ ref), rel=1e-5)
+
+
+def test_solve_level_parity_longest_history(c1):
+    # the solver's speculative pair + gradient products with 2 (m + 1) = 66 history vectors
+    p, cfg = c1
+    G = gpu_problem(p, max_iter=60, lbfgs_m=32, alpha=1.0)
+    C = cpu_problem(p, alpha=1.0)
+    D = G.zeros(0)
+    st = G.solve_level(0, D)
+    Dc, stc = C.solve_level(np.zeros(G.disp_shape(0)), m=32, max_iter=60)
+    rms = float(np.sqrt(((D.cpu().numpy() - Dc) ** 2).mean()))
+    assert rms <= 0.05, (rms, st, stc)
 
 
 @pytest.mark.parametrize("loss", [1, 0])
