@@ -3,9 +3,9 @@
 // solves, behind the C ABI declared in include/octmc.h.
 //
 // All vectors of the optimiser (displacements, gradients, directions, the
-// L-BFGS history) live in device memory; the host only reads the few
-// scalars the line search and the compact L-BFGS algebra need (f, grad .
-// dir, and 4m+5 dot products per iteration).
+// float32 L-BFGS history) live in device memory; the host only reads the
+// few scalars the line search and the compact L-BFGS algebra need (f,
+// grad . dir, and at most 4m+7 dot products per iteration).
 #include <algorithm>
 #include <chrono>
 #include <deque>
