@@ -359,7 +359,9 @@ def run_ours(args):
         torch.cuda.synchronize()
         solve = {"seconds_per_pair": time.perf_counter() - t0, "levels": levels,
                  "evals": int(sum(s["evals"] for s in stats)), "iters": [s["iters"] for s in stats],
-                 "status": [s["status"] for s in stats]}
+                 "status": [s["status"] for s in stats],
+                 "level_seconds": [round(float(s["seconds"]), 5) for s in stats],
+                 "level_evals": [int(s["evals"]) for s in stats]}
 
     # ---- rough axial prealignment of the pair (stage 1: per-B-scan offsets and tilts, all levels)
     prealign = None
