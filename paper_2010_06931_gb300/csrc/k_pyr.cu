@@ -41,8 +41,7 @@ __global__ void unpad_depth_kernel(const T* vol, int64_t columns, int d, int dp,
   }
 }
 
-// float32 -> storage type, round to nearest even.
-__device__ __forceinline__ void store_as(float* p, float v) { *p = v; }
+// float32 -> 16-bit storage type, round to nearest even.
 __device__ __forceinline__ void store_as(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 __device__ __forceinline__ void store_as(__half* p, float v) { *p = __float2half_rn(v); }
 
