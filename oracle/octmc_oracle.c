@@ -708,6 +708,26 @@ int oracle_solve_level(const oracle_level *P, double *x, const oracle_solver *op
     return lbfgs_minimize(6L * P->w * P->h, x, level_fg, (void *)P, opt, st);
 }
 
+/* The minimiser above on a caller-supplied objective fn(n, x, f, g), so the
+ * L-BFGS and its line search (Sec. 2.1) can be checked on their own. */
+typedef struct {
+    void (*fn)(long n, const double *x, double *f, double *g);
+    long n;
+} fn_ctx;
+
+static void fn_fg(void *ctx, const double *x, double *f, double *g)
+{
+    const fn_ctx *c = (const fn_ctx *)ctx;
+    c->fn(c->n, x, f, g);
+}
+
+int oracle_lbfgs_minimize_fn(long n, double *x, void (*fn)(long, const double *, double *, double *),
+                             const oracle_solver *opt, oracle_stats *st)
+{
+    fn_ctx c = {fn, n};
+    return lbfgs_minimize(n, x, fn_fg, (void *)&c, opt, st);
+}
+
 /* Number of threads the OpenMP loops use (1 without OpenMP). */
 int oracle_num_threads(void)
 {

@@ -47,6 +47,10 @@ class _Stats(C.Structure):
     _fields_ = [("iters", C.c_int), ("evals", C.c_int), ("status", C.c_int), ("f", C.c_double)]
 
 
+# objective callback of the stand-alone minimiser: fn(n, x, f, g)
+_FG = C.CFUNCTYPE(None, C.c_long, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double))
+
+
 def build(force=False):
     """Compile the oracle shared library (gcc, OpenMP) if it is missing or stale."""
     with _lock:
@@ -91,6 +95,8 @@ def _load():
                                            C.POINTER(_Stats)]
         lib.oracle_solve_level.restype = C.c_int
         lib.oracle_num_threads.restype = C.c_int
+        lib.oracle_lbfgs_minimize_fn.argtypes = [C.c_long, _dp, _FG, C.POINTER(_Solver), C.POINTER(_Stats)]
+        lib.oracle_lbfgs_minimize_fn.restype = C.c_int
         lib.oracle_merge.argtypes = [C.POINTER(_Level), _dp, C.c_double, C.c_double] + [C.c_void_p] * 5 + [C.c_void_p]
         lib.oracle_prealign_disp.argtypes = [C.POINTER(_Level), _dp, _dp]
         lib.oracle_prealign_eval.argtypes = [C.POINTER(_Level), _dp, C.POINTER(C.c_double), C.c_void_p, C.c_void_p]
@@ -219,6 +225,25 @@ def lbfgs_direction(S, Y, g):
     out = np.zeros_like(g)
     _load().oracle_lbfgs_direction(g.size, k, sp, yp, g, out)
     return out
+
+
+def lbfgs_minimize(fg, x0, m=8, max_iter=200, max_ls=20, gtol=1e-6, ftol=1e-9):
+    """The oracle's L-BFGS (the level solver's minimiser) on fg(x) -> (f, g)
+    from x0; returns (x, stats dict)."""
+    x = np.array(x0, dtype=np.float64).ravel()
+    n = x.size
+
+    def cb(n_, xp, fp, gp):
+        xv = np.ctypeslib.as_array(xp, shape=(n_,)).copy()
+        f, g = fg(xv)
+        fp[0] = float(f)
+        np.ctypeslib.as_array(gp, shape=(n_,))[:] = np.asarray(g, dtype=np.float64).ravel()
+
+    cfn = _FG(cb)
+    opt = _Solver(m, max_iter, max_ls, gtol, ftol)
+    st = _Stats()
+    _load().oracle_lbfgs_minimize_fn(n, x, cfn, C.byref(opt), C.byref(st))
+    return x, {"iters": st.iters, "evals": st.evals, "status": st.status, "f": st.f}
 
 
 # ---------------------------------------------------------------- problem

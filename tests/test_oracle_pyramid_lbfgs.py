@@ -1,9 +1,12 @@
-"""Pins of the oracle's pyramid, prolongation and L-BFGS direction (CPU only).
+"""Pins of the oracle's pyramid, prolongation, L-BFGS direction and L-BFGS
+minimiser (CPU only).
 
 Sec. 2.1: a factor-2 multi-resolution pyramid, zero displacements at the
 coarsest level, L-BFGS per level.  Readings (box mean, centre-aligned
-bilinear prolongation, two-loop recursion) are pinned by closed forms and by
-properties the mathematics fixes (the secant equation of the BFGS update).
+bilinear prolongation, two-loop recursion, weak-Wolfe bisection line search
+and its stopping rules) are pinned by closed forms, by properties the
+mathematics fixes (the secant equation of the BFGS update) and by textbook
+minimisation problems with known minimisers.
 """
 import numpy as np
 import pytest
@@ -78,3 +81,63 @@ def test_lbfgs_direction_properties():
     Vm = np.eye(n) - rho * np.outer(y, s)
     H = Vm.T @ (gam * np.eye(n)) @ Vm + rho * np.outer(s, s)
     assert np.allclose(O.lbfgs_direction([s], [y], g), -H @ g, rtol=1e-12, atol=1e-12)
+
+
+def _quadratic(a, b, offset=0.0):
+    # f = offset + 1/2 x'Ax - b'x with A = diag(a): minimiser b / a
+    return lambda x: (offset + 0.5 * x @ (a * x) - b @ x, a * x - b)
+
+
+def _rosenbrock(x):
+    r = x[1] - x[0] ** 2
+    return 100.0 * r * r + (1.0 - x[0]) ** 2, np.array([-400.0 * x[0] * r - 2.0 * (1.0 - x[0]), 200.0 * r])
+
+
+def test_lbfgs_minimize_quadratic_reaches_the_closed_form_minimiser():
+    rng = np.random.default_rng(3)
+    a, b = rng.uniform(1.0, 10.0, 50), rng.normal(size=50)
+    x, st = O.lbfgs_minimize(_quadratic(a, b), np.zeros(50), gtol=1e-10, ftol=0.0)
+    assert st["status"] == 0 and st["iters"] < 200
+    assert np.allclose(x, b / a, rtol=0.0, atol=1e-9)
+
+
+def test_lbfgs_minimize_rosenbrock():
+    # the textbook start (-1.2, 1); minimiser (1, 1)
+    x, st = O.lbfgs_minimize(_rosenbrock, [-1.2, 1.0], gtol=1e-6, ftol=0.0, max_iter=500)
+    assert st["status"] == 0, st
+    assert np.allclose(x, [1.0, 1.0], rtol=0.0, atol=1e-5)
+    assert st["f"] < 1e-10
+
+
+def test_lbfgs_first_trial_is_a_unit_step_along_minus_g():
+    # empty history: the first trial point is x0 - g0 / ||g0||_2
+    rng = np.random.default_rng(5)
+    a, b = rng.uniform(1.0, 4.0, 7), rng.normal(size=7)
+    fg = _quadratic(a, b)
+    seen = []
+
+    def rec(x):
+        seen.append(x.copy())
+        return fg(x)
+
+    x0 = rng.normal(size=7)
+    O.lbfgs_minimize(rec, x0, max_iter=1, gtol=0.0, ftol=0.0)
+    g0 = fg(x0)[1]
+    assert np.allclose(seen[0], x0, rtol=0.0, atol=0.0)
+    assert np.allclose(seen[1], x0 - g0 / np.linalg.norm(g0), rtol=0.0, atol=1e-14)
+
+
+def test_lbfgs_iteration_cap_and_relative_decrease_stops():
+    x, st = O.lbfgs_minimize(_rosenbrock, [-1.2, 1.0], max_iter=5, gtol=0.0, ftol=0.0)
+    assert st["status"] == 1 and st["iters"] == 5
+    # a large constant offset makes every relative decrease smaller than ftol:
+    # the solve stops (status 0) after 3 such iterations, before max|g| <= gtol
+    rng = np.random.default_rng(6)
+    a, b = rng.uniform(1.0, 10.0, 20), rng.normal(size=20)
+    fg = _quadratic(a, b, offset=1e12)
+    x, st = O.lbfgs_minimize(fg, np.zeros(20), gtol=1e-6, ftol=1e-9)
+    assert st["status"] == 0 and st["iters"] == 3
+    assert np.abs(fg(x)[1]).max() > 1e-6
+    # with the relative-decrease test off the same problem runs on to the gradient test
+    x, st = O.lbfgs_minimize(_quadratic(a, b), np.zeros(20), gtol=1e-6, ftol=0.0)
+    assert st["status"] == 0 and st["iters"] > 3 and np.abs(_quadratic(a, b)(x)[1]).max() <= 1e-6
