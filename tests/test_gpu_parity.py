@@ -127,6 +127,24 @@ def test_nonfinite_displacement_is_reported(c1):
     assert e.value.code == -4
 
 
+def test_nonfinite_inputs_are_reported(c1):
+    # a NaN voxel in a volume reaches the objective (non-finite f, -4); a non-finite
+    # acquisition time is rejected when the problem is created (-1)
+    import paper_2010_06931_gb300 as octmc
+    p, cfg = c1
+    q = dict(p, sx=p["sx"].copy())
+    q["sx"][5, 7, 9] = np.nan
+    G = gpu_problem(q)
+    with pytest.raises(octmc.OctmcError) as e:
+        G.eval_terms(0, G.zeros(0))
+    assert e.value.code == -4
+    q = dict(p, tx=p["tx"].copy())
+    q["tx"][2, 3] = np.inf
+    with pytest.raises(octmc.OctmcError) as e:
+        gpu_problem(q)
+    assert e.value.code == -1
+
+
 def test_eval_is_deterministic(c1):
     p, cfg = c1
     G = gpu_problem(p)
