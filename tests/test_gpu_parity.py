@@ -39,6 +39,20 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def mean_term_bound(D, mu=None):
+    """Error bound of the library's mean term M = mu sum_c S_c^2, S_c the sum of
+    component c over both scans and all A-scans.  The library forms S_c from
+    float per-thread partials (152 x 256 threads, m = ceil(w h / 38912) A-scans
+    each: 2m displacements truncated to float, 2m float additions) and adds
+    the partials in float64, so |dS_c| <= (1 + m) 2^-23 sum|D_c|."""
+    h, w = D.shape[-2:]
+    mu = 1.0 / (2.0 * w * h) if not mu else mu
+    m = -(-(h * w) // (152 * 256))
+    S, A = D.sum(axis=(0, 2, 3)), np.abs(D).sum(axis=(0, 2, 3))
+    dS = (1 + m) * 2.0 ** -23 * A
+    return mu * float(np.sum(2.0 * np.abs(S) * dS + dS * dS))
+
+
 def compare_eval(p, D, eta=0.8, **kw):
     G = gpu_problem(p, **kw)
     C = cpu_problem(p, **kw)
@@ -49,7 +63,10 @@ def compare_eval(p, D, eta=0.8, **kw):
     fc, gc, tc = C.eval(D)
     assert abs(tg[4] - fc) <= F_TOL * abs(fc), (tg, tc)
     for t in range(4):
-        assert abs(tg[t] - tc[t]) <= F_TOL * max(abs(tc[t]), 1e-12 * abs(fc)), (t, tg, tc)
+        tol = F_TOL * max(abs(tc[t]), 1e-12 * abs(fc))
+        if t == 3:  # M: where the sums S_c nearly cancel, the float partials bound it
+            tol = max(tol, mean_term_bound(np.asarray(D), kw.get("mu")))
+        assert abs(tg[t] - tc[t]) <= tol, (t, tg, tc)
     err = rel_l2(g.cpu().numpy(), gc)
     assert err <= G_TOL, err
     return tg, g.cpu().numpy(), tc, gc
