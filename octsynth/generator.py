@@ -46,8 +46,9 @@ def time_maps(w, h):
 
 
 # ------------------------------------------------------------------ motion
-def _motion(rng, n_slots, drift_sigma, n_saccades, max_saccade):
-    """Eye position m(s) per slot: drift + saccades (x, y) + axial sinusoid (z)."""
+def _motion(rng, n_slots, drift_sigma, n_saccades, max_saccade, smooth_amp=0.0):
+    """Eye position m(s) per slot: drift + saccades (x, y) + axial sinusoid (z),
+    plus, with smooth_amp > 0, slow transverse sinusoids of that amplitude."""
     m = np.cumsum(rng.normal(0.0, drift_sigma, size=(n_slots, 3)), axis=0)
     sac = np.sort(rng.integers(1, n_slots, size=n_saccades))
     cur = np.zeros(2)
@@ -61,6 +62,10 @@ def _motion(rng, n_slots, drift_sigma, n_saccades, max_saccade):
         m[s:, :2] += jump
     seconds = np.arange(n_slots) * (SCAN_SECONDS / n_slots)
     m[:, 2] += AXIAL_AMP * np.sin(2.0 * math.pi * AXIAL_HZ * seconds + rng.uniform(0, 2 * math.pi))
+    if smooth_amp > 0.0:
+        for c in range(2):
+            hz, ph = rng.uniform(0.2, 0.6), rng.uniform(0, 2 * math.pi)
+            m[:, c] += smooth_amp * np.sin(2.0 * math.pi * hz * seconds + ph)
     return m, sac
 
 
@@ -157,6 +162,18 @@ def _sample_map(img, x, y):
             (1 - fu) * fv * img[v0 + 1, u0] + fu * fv * img[v0 + 1, u0 + 1])
 
 
+def _sample_grid(img, u, v):
+    """Bilinear sample of a texture given at integer positions, at continuous (u, v):
+    the texture moves with the eye as a continuous function of position."""
+    H, W = img.shape
+    u = np.clip(u, 0, W - 1.001)
+    v = np.clip(v, 0, H - 1.001)
+    u0, v0 = np.floor(u).astype(np.int64), np.floor(v).astype(np.int64)
+    fu, fv = (u - u0).astype(np.float32), (v - v0).astype(np.float32)
+    return ((1 - fu) * (1 - fv) * img[v0, u0] + fu * (1 - fv) * img[v0, u0 + 1] +
+            (1 - fu) * fv * img[v0 + 1, u0] + fu * fv * img[v0 + 1, u0 + 1])
+
+
 # ------------------------------------------------------------------ pair
 def _interp_motion(m, s):
     """Motion at continuous slot positions s (linear, clamped)."""
@@ -184,7 +201,7 @@ def _render_torch(retina, x, y, z0, d, speckle, gen, device):
 
 
 def make_pair(w, h, d, n_layers=8, n_slabs=2, n_saccades=2, max_saccade=5.0, drift_sigma=0.02,
-              seed=0, speckle=True, row_chunk=16, device=None, **_unused):
+              seed=0, speckle=True, row_chunk=16, device=None, smooth_amp=0.0, angio_noise=True, **_unused):
     """Render one orthogonal scan pair.
 
     Returns a dict with float32 ``sx, sy [h][w][d]``, ``ax, ay [h][w]``,
@@ -198,8 +215,8 @@ def make_pair(w, h, d, n_layers=8, n_slabs=2, n_saccades=2, max_saccade=5.0, dri
     retina = _Retina(rng, w, h, d, n_layers)
     fx, fy = slots(w, h)
     nx, ny = h * (w + fx), w * (h + fy)
-    mx, sacx = _motion(rng, nx, drift_sigma, n_saccades, max_saccade)
-    my, sacy = _motion(rng, ny, drift_sigma, n_saccades, max_saccade)
+    mx, sacx = _motion(rng, nx, drift_sigma, n_saccades, max_saccade, smooth_amp)
+    my, sacy = _motion(rng, ny, drift_sigma, n_saccades, max_saccade, smooth_amp)
     tx, ty = time_maps(w, h)
 
     slab_maps = [_rasterise(_vessel_segments(rng, w, h), w, h) for _ in range(n_slabs)]
@@ -237,10 +254,10 @@ def make_pair(w, h, d, n_layers=8, n_slabs=2, n_saccades=2, max_saccade=5.0, dri
         s = tmap.astype(np.int64)
         jj, ii = np.meshgrid(np.arange(h), np.arange(w), indexing="ij")
         a = angio_at(ii + m[s, 0], jj + m[s, 1])
-        bgx = np.clip(ii + m[s, 0] + ANGIO_PAD, 0, w + 2 * ANGIO_PAD - 1).astype(np.int64)
-        bgy = np.clip(jj + m[s, 1] + ANGIO_PAD, 0, h + 2 * ANGIO_PAD - 1).astype(np.int64)
-        a += np.float32(0.02) * angio_bg[bgy, bgx]
-        a += srng.normal(0.0, 0.01, size=a.shape).astype(np.float32)
+        noise = srng.normal(0.0, 0.01, size=a.shape).astype(np.float32)
+        if angio_noise:
+            a += np.float32(0.02) * _sample_grid(angio_bg, ii + m[s, 0] + ANGIO_PAD, jj + m[s, 1] + ANGIO_PAD)
+            a += noise
         # saccades: B-scans within 2 of a jump are saturated and invalid (Sec. 2.2)
         valid = np.ones(slow_len, dtype=np.float32)
         fast = w + fx if name == "x" else h + fy
@@ -282,8 +299,11 @@ def true_displacement(pair, w, h, iters=60):
 
     Solves p + d + m(t(p + d)) = p + c by damped fixed-point iteration, with the
     slot map extended linearly between A-scans; c makes the total displacement
-    zero per component.  A-scans within 2 B-scans of a saccade are masked out
-    (the solution there is not unique).
+    zero per component.  A-scans near a saccade are masked out (the solution
+    there is not unique): the B-scans within 2 of the saccade, and, in the
+    corrected frame, the band of slow-axis positions between where the
+    saccade's B-scan lands before and after the jump (the gap or the overlap
+    the jump leaves), widened by 2.5 B-scans on both sides.
     """
     fx, fy = slots(w, h)
     jj, ii = np.meshgrid(np.arange(h, dtype=np.float64), np.arange(w, dtype=np.float64), indexing="ij")
@@ -308,4 +328,15 @@ def true_displacement(pair, w, h, iters=60):
                 else:
                     mask[V, :, max(0, b - 2):b + 3] = False
         c = c - disp.mean(axis=(0, 2, 3))
+    # the gap / overlap band of each saccade in the corrected frame: acquired
+    # slow position b shows the object at b + m_slow - c_slow
+    for V, (m, sac) in enumerate(((pair["mx"], pair["sacx"]), (pair["my"], pair["sacy"]))):
+        fast = w + fx if V == 0 else h + fy
+        slow = 1 if V == 0 else 0
+        pos = jj if V == 0 else ii
+        for sl in sac:
+            b = sl / fast
+            lo = b + min(m[sl - 1, slow], m[sl, slow]) - c[slow] - 2.5
+            hi = b + max(m[sl - 1, slow], m[sl, slow]) - c[slow] + 2.5
+            mask[V] &= ~((pos >= lo) & (pos <= hi))
     return disp, mask

@@ -13,7 +13,7 @@ adds the multi-resolution driver (pyramid -> per-level eta -> L-BFGS ->
 prolongation), Sec. 2.1 of Ploner et al. (arXiv 2010.06931).
 """
 from .oracle import (  # noqa: F401
-    OracleProblem, build, cr_weights, interp1, interp2, interp3, loss, chain,
+    OracleProblem, build, cr_weights, interp1, validity_interp, interp2, interp3, loss, chain,
     pyramid_volume, pyramid_image, pyramid_line, pyramid_time, prolong,
     lbfgs_direction, lbfgs_minimize, num_threads, LOSS_PSEUDO_HUBER, LOSS_SSD, prealign_prolong,
     saccade_validity, median3, rank_filter, percentile, bscan_median_subtract, replace_invalid, enface,

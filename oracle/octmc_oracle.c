@@ -21,7 +21,10 @@
  *   - en-face angio residual and S^ang                       [Eq. 6]
  *   - combined similarity with eta, and eta itself           [Eq. 9, 10]
  *   - temporal regulariser R and mean term M (readings: the  [Sec. 2.1]
- *     paper defers their exact form to earlier work)
+ *     paper defers their exact form to earlier work; R carries the
+ *     level depth d like the angio term of Eq. 6)
+ *   - validity resampled by a Hermite interpolant without      [Eq. 7, 8]
+ *     overshoot, so that 0 <= delta <= delta_0
  *   - the analytic gradient of all of the above (chain rule)
  *   - factor-2 pyramid, displacement prolongation, and the   [Sec. 2.1]
  *     L-BFGS solve with a weak-Wolfe bisection line search
@@ -118,6 +121,27 @@ double oracle_interp1(const float *v, int n, double u, double *du)
     }
     if (du) *du = der;
     return val;
+}
+
+/* Validity resampling (Sec. 2.2, Eq. 7-8).  The paper asks for a Hermite
+ * interpolant with continuous first derivatives, and states that delta is
+ * delta_0 where both scans are valid, 0 where one is invalid, and fades
+ * smoothly in between.  Central-difference tangents overshoot a 0/1 step
+ * (delta would become negative next to an invalid band), so this reading
+ * takes the cubic Hermite interpolant with zero tangents at the nodes: on
+ * [n, n+1] the value is p_n + (p_{n+1} - p_n) (3 t^2 - 2 t^3).  It is C^1,
+ * passes through the nodes and stays between the two node values.  Samples
+ * outside the line replicate the edge value. */
+double oracle_validity_interp(const float *v, int n, double u, double *du)
+{
+    long b;
+    double t;
+    split_coord(u, n, &b, &t);
+    double p0 = v[clampl(b, n)], p1 = v[clampl(b + 1, n)];
+    double h = t * t * (3.0 - 2.0 * t);   /* Hermite basis h01 */
+    double dh = 6.0 * t * (1.0 - t);
+    if (du) *du = (p1 - p0) * dh;
+    return p0 + (p1 - p0) * h;
 }
 
 /* 2-D interpolation of an image img[h][w] at (x, y); gradient to g[2]. */
@@ -229,8 +253,8 @@ static void ascan_terms(const oracle_level *P, const double *disp, int i, int j,
 
     /* Eq. 7: validity resampled along each scan's slow axis. */
     double vtx = 1.0, dvtx = 0.0, vty = 1.0, dvty = 0.0;
-    if (P->vx) vtx = oracle_interp1(P->vx, h, (double)j + dX[1], &dvtx);
-    if (P->vy) vty = oracle_interp1(P->vy, w, (double)i + dY[0], &dvty);
+    if (P->vx) vtx = oracle_validity_interp(P->vx, h, (double)j + dX[1], &dvtx);
+    if (P->vy) vty = oracle_validity_interp(P->vy, w, (double)i + dY[0], &dvty);
     /* Eq. 8 */
     double delta = delta0 * vtx * vty;
 
@@ -345,7 +369,16 @@ void oracle_chain(const double *t, long n, long *order, double *omega)
     }
 }
 
-/* R(D) and, if grad != NULL, adds alpha * dR/dD into grad. */
+/* R(D) and, if grad != NULL, adds alpha * dR/dD into grad.
+ *
+ * Scale reading: each pair's penalty is multiplied by the depth d of the
+ * level.  The structural data term sums d voxels per A-scan (Eq. 3, 5), and
+ * Eq. 6 multiplies the per-A-scan angiographic loss by d for exactly this
+ * reason; R is a per-A-scan quantity as well, so it carries the same factor.
+ * Then alpha weighs the regulariser against the data term in the same ratio
+ * on every pyramid level (d halves with the voxel count per A-scan), and
+ * the paper's alpha values (0.001 ... 1, Sec. 4) change the result, which
+ * they do not with an unscaled R (its size is that of one voxel per A-scan). */
 static double regulariser(const oracle_level *P, const double *disp, double *grad)
 {
     const int w = P->w, h = P->h;
@@ -360,10 +393,10 @@ static double regulariser(const oracle_level *P, const double *disp, double *gra
             for (int c = 0; c < 3; c++) {
                 long ip = ((long)V * 3 + c) * n + p, iq = ((long)V * 3 + c) * n + q;
                 double dl;
-                R += omega[m] * oracle_loss(disp[iq] - disp[ip], P->eps_r, OR_LOSS_PSEUDO_HUBER, &dl);
+                R += P->d * omega[m] * oracle_loss(disp[iq] - disp[ip], P->eps_r, OR_LOSS_PSEUDO_HUBER, &dl);
                 if (grad) {
-                    grad[iq] += P->alpha * omega[m] * dl;
-                    grad[ip] -= P->alpha * omega[m] * dl;
+                    grad[iq] += P->alpha * P->d * omega[m] * dl;
+                    grad[ip] -= P->alpha * P->d * omega[m] * dl;
                 }
             }
         }
@@ -831,8 +864,8 @@ void oracle_merge(const oracle_level *P, const double *disp, double beta, double
                 double gdummy[2], AXv, AYv;
                 AXv = oracle_interp2(P->ax, w, h, i + dget(disp, w, h, 0, 0, i, j), j + dget(disp, w, h, 0, 1, i, j), gdummy);
                 AYv = oracle_interp2(P->ay, w, h, i + dget(disp, w, h, 1, 0, i, j), j + dget(disp, w, h, 1, 1, i, j), gdummy);
-                if (P->vx) va[0] = oracle_interp1(P->vx, h, j + dget(disp, w, h, 0, 1, i, j), NULL);
-                if (P->vy) va[1] = oracle_interp1(P->vy, w, i + dget(disp, w, h, 1, 0, i, j), NULL);
+                if (P->vx) va[0] = oracle_validity_interp(P->vx, h, j + dget(disp, w, h, 0, 1, i, j), NULL);
+                if (P->vy) va[1] = oracle_validity_interp(P->vy, w, i + dget(disp, w, h, 1, 0, i, j), NULL);
                 double a0 = fmax(0.0, c0 * va[0]), a1 = fmax(0.0, c1 * va[1]);
                 angio[p] = (a0 + a1 > 0) ? (float)((a0 * AXv + a1 * AYv) / (a0 + a1)) : 0.0f;
             }

@@ -70,6 +70,8 @@ def _load():
         lib.oracle_cr_weights.argtypes = [C.c_double, _dp, _dp]
         lib.oracle_interp1.argtypes = [_fp, C.c_int, C.c_double, C.POINTER(C.c_double)]
         lib.oracle_interp1.restype = C.c_double
+        lib.oracle_validity_interp.argtypes = [_fp, C.c_int, C.c_double, C.POINTER(C.c_double)]
+        lib.oracle_validity_interp.restype = C.c_double
         lib.oracle_interp2.argtypes = [_fp, C.c_int, C.c_int, C.c_double, C.c_double, _dp]
         lib.oracle_interp2.restype = C.c_double
         lib.oracle_interp3.argtypes = [_fp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
@@ -132,6 +134,14 @@ def interp1(v, u):
     v = np.ascontiguousarray(v, dtype=np.float32)
     du = C.c_double()
     val = _load().oracle_interp1(v, v.shape[0], float(u), C.byref(du))
+    return val, du.value
+
+
+def validity_interp(v, u):
+    """Validity line resampled at u (Eq. 7): (value, d value / du)."""
+    v = np.ascontiguousarray(v, dtype=np.float32)
+    du = C.c_double()
+    val = _load().oracle_validity_interp(v, v.shape[0], float(u), C.byref(du))
     return val, du.value
 
 

@@ -143,3 +143,52 @@ def test_loss_closed_forms():
     # small-|x| limit of pseudo-Huber is x^2 / (2 eps), i.e. SSD / (2 eps)
     v, _ = O.loss(1e-7, eps)
     assert v == pytest.approx(1e-14 / (2 * eps), rel=1e-6)
+
+
+# ---------------------------------------------------------------- validity (Eq. 7, 8)
+# Reading: the validity line is resampled by the cubic Hermite interpolant
+# with zero node tangents, so that delta stays within [0, delta_0]: 0 where a
+# scan is invalid, delta_0 where both are valid, a smooth fade in between
+# (Sec. 2.2).  Pinned by the properties that fix it: it passes through the
+# nodes with zero slope there (C^1 across nodes), never leaves the range of
+# its two nodes, is the Hermite basis function 3 t^2 - 2 t^3 on a unit step,
+# and replicates the edge samples.
+
+def test_validity_nodes_slope_and_edges():
+    rng = np.random.default_rng(3)
+    v = rng.uniform(0, 1, 9).astype(np.float32)
+    for n in range(9):
+        val, du = O.validity_interp(v, float(n))
+        assert val == float(v[n]) and du == 0.0
+    for u in (-3.0, -1.0, -0.25):
+        assert O.validity_interp(v, u) == (float(v[0]), 0.0)
+    for u in (8.0, 8.6, 11.0):
+        assert O.validity_interp(v, u) == (float(v[8]), 0.0)
+
+
+def test_validity_step_is_the_hermite_basis_and_never_overshoots():
+    v = np.array([0, 0, 0, 1, 1, 1], dtype=np.float32)
+    for t in np.linspace(0.0, 1.0, 41):
+        val, du = O.validity_interp(v, 2.0 + t)
+        assert val == pytest.approx(t * t * (3 - 2 * t), abs=1e-15)
+        assert du == pytest.approx(6 * t * (1 - t), abs=1e-14)
+    # the Catmull-Rom interpolant of the same step dips below 0 between the zeros
+    assert O.interp1(v, 1.5)[0] < -0.05
+    rng = np.random.default_rng(4)
+    w = (rng.uniform(size=30) > 0.4).astype(np.float32)
+    for u in rng.uniform(-2, 31, 400):
+        val, _ = O.validity_interp(w, u)
+        b = int(np.clip(np.floor(u), 0, 29))
+        lo, hi = sorted((float(w[b]), float(w[min(b + 1, 29)])))
+        assert lo <= val <= hi
+
+
+def test_validity_derivative_matches_central_differences():
+    rng = np.random.default_rng(5)
+    v = rng.uniform(0, 1, 12).astype(np.float32)
+    for u in rng.uniform(0.05, 10.95, 50):
+        if abs(u - round(u)) < 1e-3:
+            continue
+        e = 1e-6
+        fd = (O.validity_interp(v, u + e)[0] - O.validity_interp(v, u - e)[0]) / (2 * e)
+        assert O.validity_interp(v, u)[1] == pytest.approx(fd, rel=1e-7, abs=1e-9)

@@ -159,7 +159,9 @@ def test_regulariser_and_mean_closed_forms():
     D[1, 2] = 1.5                        # Y volume, z component: constant
     f, g, t = P.eval(D)
     Lr = lambda x: O.loss(x, 0.5)[0]
-    R_ref = h * (w - 1) * Lr(a) + (h - 1) * Lr(-a * (w - 1)) / 4.0
+    # every pair of the time chain carries the level depth d (the per-A-scan
+    # scale of the data term, as in Eq. 6); flyback steps weigh 1/(1 + 3)
+    R_ref = d * (h * (w - 1) * Lr(a) + (h - 1) * Lr(-a * (w - 1)) / 4.0)
     assert t[2] == pytest.approx(R_ref, rel=1e-13)
     sx_sum = D[0, 0].sum()
     M_ref = 0.25 * (sx_sum ** 2 + (1.5 * w * h) ** 2)
@@ -176,7 +178,8 @@ def translation_problem(loss, eps_h):
     t = np.array([2.0, -2.0, 2.0])
     sx, sy = render(obj, shape, -t / 2), render(obj, shape, t / 2)
     tx, ty = raster_times(w, h, 4)
-    P = O.OracleProblem(sx, sy, tx, ty, alpha=0.1, eps_h=eps_h, eps_r=0.5, loss=loss)
+    # R carries the depth d; alpha = 0.1 / d keeps the regulariser at 0.1 per pair
+    P = O.OracleProblem(sx, sy, tx, ty, alpha=0.1 / d, eps_h=eps_h, eps_r=0.5, loss=loss)
     sol = np.zeros(P.shape_disp())
     for c in range(3):
         sol[0, c], sol[1, c] = t[c] / 2, -t[c] / 2
@@ -202,6 +205,53 @@ def test_translation_recovered_by_the_solver():
     assert np.abs(rel[:, 4:-4, 4:-4]).max() < 0.03
     assert np.sqrt(((D - sol) ** 2).mean()) < 0.6
     assert st["f"] < 1e-3 * P.eval(np.zeros(P.shape_disp()), grad=False)[0]
+
+
+def test_delta_stays_between_zero_and_delta0():
+    # Sec. 2.2: delta is delta_0 where both scans are valid, 0 where one is
+    # invalid and fades smoothly in between.  Every A-scan of a 1 x h grid
+    # samples the X validity at the same position u (dy^X = u - j), with
+    # identical volumes and equal displacements (S^str = 0) and angio images
+    # 1 and 0 (L(R_a) = L(1) everywhere), so S^ang = h d delta(u) L(1).
+    h, d = 6, 4
+    s = np.zeros((h, 1, d), dtype=np.float32)
+    tx, ty = raster_times(1, h, 1)
+    vx = np.array([1, 1, 0, 0, 1, 1], dtype=np.float32)
+    P = O.OracleProblem(s, s, tx, ty, np.ones((h, 1)), np.zeros((h, 1)), vx, np.ones(1), alpha=0.0, mu=0.0)
+    L1 = O.loss(1.0, 1e-3)[0]
+    for u in np.linspace(-1.0, 6.0, 57):
+        D = np.zeros(P.shape_disp())
+        D[:, 1, :, 0] = u - np.arange(h)
+        _, _, t = P.eval(D, grad=False)
+        delta = t[1] / (h * d * L1)
+        assert -1e-15 <= delta <= 0.5 + 1e-15
+        if 2.0 <= u <= 3.0:
+            assert delta == 0.0  # between two invalid B-scans
+        if u <= 1.0 or u >= 4.0:
+            assert delta == pytest.approx(0.5, abs=1e-15)
+
+
+def test_known_motion_recovered_from_zero():
+    # The method's purpose (Sec. 2.1, Eq. 1): from zero displacement, the
+    # coarse-to-fine L-BFGS solve recovers known motion.  Noise-free rendering
+    # of the c1 scan pair (drift and the 1 Hz axial sinusoid; no speckle, no
+    # angiography noise, no saccades, so the truth is unique), the paper's
+    # alpha = 0.1 and delta_0 = 0.5, three levels, each solved to the ftol
+    # stopping rule.  Bar: 0.2 px RMS against the true field (A-scans more
+    # than 4 px from the border), 0.2 px on the data-determined relative mode.
+    p, cfg = make_config("c1", speckle=False, angio_noise=False, n_saccades=0)
+    T, mask = true_displacement(p, cfg["w"], cfg["h"])
+    mask[:, :4] = mask[:, -4:] = False
+    mask[:, :, :4] = mask[:, :, -4:] = False
+    m6 = np.broadcast_to(mask[:, None], T.shape)
+    assert np.sqrt((T[m6] ** 2).mean()) > 1.0  # the motion to recover
+    P = problem(p)
+    D, stats = P.solve_full(3, max_iter=3000, ftol=1e-6)
+    assert [s["status"] for s in stats] == [0, 0, 0]
+    assert np.sqrt(((D - T)[m6] ** 2).mean()) < 0.2
+    both = mask[0] & mask[1]
+    rel = (D[0] - D[1]) - (T[0] - T[1])
+    assert np.sqrt((rel[:, both] ** 2).mean()) < 0.2
 
 
 def test_known_motion_minimum_is_near_the_truth():
