@@ -21,6 +21,12 @@
  *    [volume X,Y][component dx,dy,dz][j][i] of level l (Sec. 2.1: one
  *    3-D displacement per A-scan and volume).
  *  - Objective (Eq. 1 with Eq. 9): f = eta*S^str + S^ang/eta + alpha*R + M.
+ *    R sums, over each scan's time-ordered A-scans, the pseudo-Huber penalty
+ *    of consecutive displacement differences (flyback steps weighted lower)
+ *    times the level depth d, the per-A-scan scale of the data term that
+ *    Eq. 6 also applies to the angio term.  The validity of Eq. 7 is
+ *    resampled by the Hermite interpolant with zero node tangents, so
+ *    0 <= delta <= delta_0 (Eq. 8).
  *  - Every call is ordered on the problem's CUDA stream; "device" pointers
  *    are CUDA global memory the caller owns; "host" pointers are ordinary
  *    memory.  Calls on one problem are not thread-safe.  An evaluation forks
@@ -72,10 +78,10 @@ typedef struct {
     int loss;             /* octmc_loss                                                */
     int levels;           /* pyramid levels, >= 1 (factor 2 each, Sec. 2.1)            */
     int lbfgs_m;          /* L-BFGS history length, 1..32 (default 8)                  */
-    int max_iter;         /* L-BFGS iterations per level                               */
+    int max_iter;         /* L-BFGS iterations per level (default 5000)                */
     int max_ls;           /* objective evaluations per line search                     */
     double gtol;          /* stop when max|grad| <= gtol                               */
-    double ftol;          /* stop after 3 iterations with relative decrease < ftol     */
+    double ftol;          /* stop after 3 iterations of relative decrease < ftol (1e-7) */
     void *stream;         /* cudaStream_t (NULL = the legacy default stream)           */
 } octmc_desc;
 
@@ -255,11 +261,9 @@ int octmc_level_data(const octmc_problem *p, int level, float *sx, float *sy, fl
 /* ---------------------------------------------------------------------
  * Stand-alone L-BFGS (Sec. 2.1) over n float64 device values: the compact
  * representation of the inverse Hessian with gamma = s'y / y'y of the latest
- * pair; pairs with s'y <= 1e-12 y'y are rejected.  The pairs are stored
- * rounded to float32 and their products with y and g are float32 FMAs summed
- * in float64 across warps and blocks (about 1e-8 relative on the direction
- * for well-conditioned histories); g'g, max|g| and the -gamma g term of the
- * direction are float64, so an empty history gives exactly -g.  m is 1..32.
+ * pair; pairs with s'y <= 1e-12 y'y are rejected.  The pairs, every product
+ * with them and every sum are float64 (fixed reduction order, so results are
+ * reproducible); an empty history gives exactly -g.  m is 1..32.
  * --------------------------------------------------------------------- */
 typedef struct octmc_lbfgs octmc_lbfgs;
 

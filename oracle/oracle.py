@@ -322,7 +322,7 @@ class OracleProblem:
         L = self._level()
         return _load().oracle_eta(C.byref(L), disp0)
 
-    def solve_level(self, disp, m=8, max_iter=200, max_ls=20, gtol=1e-6, ftol=1e-9, set_eta=True):
+    def solve_level(self, disp, m=8, max_iter=5000, max_ls=20, gtol=1e-6, ftol=1e-7, set_eta=True):
         """L-BFGS solve of this level from disp; returns (disp, stats dict)."""
         x = np.array(disp, dtype=np.float64, order="C", copy=True)
         if set_eta:

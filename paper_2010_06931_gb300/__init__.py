@@ -61,7 +61,7 @@ class Problem:
 
     def __init__(self, sx, sy, tx, ty, ax=None, ay=None, vx=None, vy=None, *, storage=F32,
                  alpha=0.1, delta0=0.5, eps_h=1e-3, eps_r=1e-2, mu=0.0, loss=LOSS_PSEUDO_HUBER,
-                 levels=1, lbfgs_m=8, max_iter=200, max_ls=20, gtol=1e-6, ftol=1e-9):
+                 levels=1, lbfgs_m=8, max_iter=5000, max_ls=20, gtol=1e-6, ftol=1e-7):
         L = N.lib()
         arrays = [sx, sy, tx, ty, ax, ay, vx, vy]
         on_dev = all(isinstance(a, torch.Tensor) and a.is_cuda for a in arrays if a is not None)
@@ -364,7 +364,7 @@ class Server:
 
     def submit(self, sx, sy, tx, ty, ax=None, ay=None, vx=None, vy=None, *, storage=F32, alpha=0.1,
                delta0=0.5, eps_h=1e-3, eps_r=1e-2, mu=0.0, loss=LOSS_PSEUDO_HUBER, levels=1, lbfgs_m=8,
-               max_iter=200, max_ls=20, gtol=1e-6, ftol=1e-9):
+               max_iter=5000, max_ls=20, gtol=1e-6, ftol=1e-7):
         arrays = [sx, sy, tx, ty, ax, ay, vx, vy]
         on_dev = all(isinstance(a, torch.Tensor) and a.is_cuda for a in arrays if a is not None)
         dev = torch.device("cuda") if on_dev else torch.device("cpu")

@@ -3,7 +3,7 @@
 // solves, behind the C ABI declared in include/octmc.h.
 //
 // All vectors of the optimiser (displacements, gradients, directions, the
-// float32 L-BFGS history) live in device memory; the host only reads the
+// L-BFGS history, all float64) live in device memory; the host only reads the
 // few scalars the line search and the compact L-BFGS algebra need (f,
 // grad . dir, and at most 4m+7 dot products per iteration).
 #include <algorithm>
@@ -105,7 +105,7 @@ struct octmc_lbfgs {
   int64_t n = 0;
   int m = 0;
   cudaStream_t st = nullptr;
-  std::vector<float*> S, Y;   // m + 1 buffers each (float32 pairs)
+  std::vector<double*> S, Y;  // m + 1 buffers each
   std::vector<int> order;     // stored pairs, oldest first (buffer ids)
   int spare = 0;              // buffer receiving the next pair
   std::vector<double> SY, YY; // (m+1)^2, indexed by buffer ids
@@ -118,8 +118,8 @@ struct octmc_lbfgs {
   double gg = 0.0, gmax = 0.0;
 
   ~octmc_lbfgs() {
-    for (float* p : S) dfree(p);
-    for (float* p : Y) dfree(p);
+    for (double* p : S) dfree(p);
+    for (double* p : Y) dfree(p);
     dfree(partials);
     dfree(counter);
     dfree(dots_dev);
@@ -133,8 +133,8 @@ struct octmc_lbfgs {
     S.assign(m + 1, nullptr);
     Y.assign(m + 1, nullptr);
     for (int b = 0; b <= m; b++) {
-      S[b] = dalloc<float>((size_t)n);
-      Y[b] = dalloc<float>((size_t)n);
+      S[b] = dalloc<double>((size_t)n);
+      Y[b] = dalloc<double>((size_t)n);
     }
     SY.assign((size_t)(m + 1) * (m + 1), 0.0);
     YY.assign((size_t)(m + 1) * (m + 1), 0.0);
@@ -281,9 +281,9 @@ struct octmc_lbfgs {
       gd = -gamma * gg;
       for (int i = 0; i < k; i++) {
         lc.h[lc.K] = S[order[i]];
-        lc.c[lc.K++] = (float)-top[i];
+        lc.c[lc.K++] = -top[i];
         lc.h[lc.K] = Y[order[i]];
-        lc.c[lc.K++] = (float)(gamma * u[i]);
+        lc.c[lc.K++] = gamma * u[i];
         gd += -top[i] * a[i] + gamma * u[i] * b[i];
       }
       if (!(gd < 0.0)) k_reset_steepest(lc, g, gd);
@@ -1216,10 +1216,10 @@ void octmc_desc_defaults(octmc_desc* d) {
   d->loss = OCTMC_LOSS_PSEUDO_HUBER;
   d->levels = 1;
   d->lbfgs_m = 8;
-  d->max_iter = 200;
+  d->max_iter = 5000;
   d->max_ls = 20;
   d->gtol = 1e-6;
-  d->ftol = 1e-9;
+  d->ftol = 1e-7;
 }
 
 int octmc_create_problem(const octmc_desc* desc, octmc_problem** out) {
@@ -1449,8 +1449,8 @@ void octmc_lbfgs_destroy(octmc_lbfgs* h) {
 int octmc_lbfgs_push(octmc_lbfgs* h, const double* s, const double* y) {
   if (!h || !s || !y) return OCTMC_ERR_INVALID_ARG;
   return guarded([&] {
-    CK(launch_to_f32(s, h->S[h->spare], h->n, h->st));
-    CK(launch_to_f32(y, h->Y[h->spare], h->n, h->st));
+    CK(cudaMemcpyAsync(h->S[h->spare], s, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(h->Y[h->spare], y, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->st));
     return h->prepare(nullptr, true);
   });
 }

@@ -28,6 +28,19 @@ __device__ __forceinline__ void keys_weights(float t, float w[4], float dw[4]) {
   dw[3] = t * fmaf(1.5f, t, -1.0f);
 }
 
+// Validity line v (n samples) at b + t, 0 <= t < 1 (Ploner et al., Sec. 2.2,
+// Eq. 7): the cubic Hermite interpolant with zero tangents at the nodes,
+// v_b + (v_{b+1} - v_b) (3 t^2 - 2 t^3), edge samples replicated.  It is C^1
+// and never leaves the range of its two nodes, so delta (Eq. 8) stays within
+// [0, delta_0] next to invalid B-scans.
+__device__ __forceinline__ void validity_hermite(const float* v, int n, int b, float t, float* val,
+                                                 float* dval) {
+  const float p0 = v[clampi(b, n)], p1 = v[clampi(b + 1, n)];
+  const float dp = p1 - p0;
+  *val = fmaf(dp, (t * t) * fmaf(-2.0f, t, 3.0f), p0);
+  *dval = dp * (6.0f * t) * (1.0f - t);
+}
+
 // Exact split of u = off + v, v a double given by its bit pattern and off an
 // integer, into floor(u) and the fraction u - floor(u) as a float (mantissa
 // truncated to 24 bits), after clamping u into the integer range [lo, hi].
@@ -269,39 +282,35 @@ cudaError_t launch_unpad_depth(const void* vol, int dtype, int64_t columns, int 
                                cudaStream_t s);
 cudaError_t launch_convert(const float* in, void* out, int dtype, int64_t n, cudaStream_t s);
 
-// L-BFGS vector kernels.  The iterate x, the gradient g and the direction
-// are float64; the history pairs (s, y) are stored in float32 (each formed
-// as a float64 difference, then rounded).  Products with the history are
-// taken in float32 (float64 runs at 1/64 of the float rate on this GPU) and
-// reduced across warps and blocks in float64 with fixed trees.
+// L-BFGS vector kernels.  The iterate x, the gradient g, the direction and
+// the history pairs (s, y) are float64, and so are all products and sums.
 constexpr int kMaxHist = 66;  // 2 (m + 1) history vectors for m <= 32
-// Dot products of K history vectors with up to two probes: q0 (float32,
-// the newest y) and q1 (float64, a gradient); a null probe reads as 0.
+// Dot products of K history vectors with up to two probes q0 (the newest y)
+// and q1 (a gradient); a null probe reads as 0.
 // Outputs: [2k] = h_k . q0, [2k+1] = h_k . q1 (k < K), [2K] = q0 . q0,
-// [2K+1] = q1 . q1 (float64 products), [2K+2] = max |q1| (exact).
+// [2K+1] = q1 . q1, [2K+2] = max |q1| (exact).
 struct HistDots {
-  const float* h[kMaxHist];
+  const double* h[kMaxHist];
   int K;
-  const float* q0;
+  const double* q0;
   const double* q1;
 };
 __host__ __device__ inline int hist_dots_outputs(int K) { return 2 * K + 3; }
-// out = cg g + sum_k c_k h_k (the g term in float64, the history sum in float32).
+// out = cg g + sum_k c_k h_k.
 struct HistComb {
   const double* g;
   double cg;
-  const float* h[kMaxHist];
-  float c[kMaxHist];
+  const double* h[kMaxHist];
+  double c[kMaxHist];
   int K;
 };
 int hist_dots_blocks(int64_t n);
 cudaError_t launch_hist_dots(const HistDots& hd, int64_t n, double* partials, unsigned* counter, double* out,
                              cudaStream_t s);
 cudaError_t launch_hist_comb(const HistComb& hc, int64_t n, double* out, cudaStream_t s);
-// s = x1 - x0, y = g1 - g0 (float64 differences rounded to float32).
+// s = x1 - x0, y = g1 - g0.
 cudaError_t launch_sub2(const double* x1, const double* x0, const double* g1, const double* g0,
-                        float* s_out, float* y_out, int64_t n, cudaStream_t st);
-cudaError_t launch_to_f32(const double* in, float* out, int64_t n, cudaStream_t s);
+                        double* s_out, double* y_out, int64_t n, cudaStream_t st);
 cudaError_t launch_axpy(const double* x, double a, const double* d, double* out, int64_t n,
                         cudaStream_t s);
 

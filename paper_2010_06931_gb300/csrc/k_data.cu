@@ -85,25 +85,11 @@ __device__ __forceinline__ void data_ascan(const DataArgs& A, int64_t p, int lan
   for (int c = 0; c < 7; c++) acc[c] = warp_sum(acc[c]);
 
   // ---- per-A-scan scalars (Eq. 6-8), float, every lane
+  // Eq. 7: X validity along y at j + dy^X, Y validity along x at i + dx^Y,
+  // by the zero-tangent Hermite interpolant (no overshoot: 0 <= delta <= delta_0)
   float vtx = 1.f, dvtx = 0.f, vty = 1.f, dvty = 0.f;
-  if (L.vx) {  // Eq. 7: X validity along y at j + dy^X (the weights of S^X in y)
-    vtx = 0.f;
-#pragma unroll
-    for (int b = 0; b < 4; b++) {
-      const float s = L.vx[clampi(VX.by - 1 + b, L.h)];
-      vtx = fmaf(VX.wy[b], s, vtx);
-      dvtx = fmaf(VX.dwy[b], s, dvtx);
-    }
-  }
-  if (L.vy) {  // Y validity along x at i + dx^Y
-    vty = 0.f;
-#pragma unroll
-    for (int a = 0; a < 4; a++) {
-      const float s = L.vy[clampi(VY.bx - 1 + a, L.w)];
-      vty = fmaf(VY.wx[a], s, vty);
-      dvty = fmaf(VY.dwx[a], s, dvty);
-    }
-  }
+  if (L.vx) validity_hermite(L.vx, L.h, VX.by, frac[1], &vtx, &dvtx);
+  if (L.vy) validity_hermite(L.vy, L.w, VY.bx, frac[3], &vty, &dvty);
   const float delta0 = (float)A.delta0;
   const float delta = delta0 * vtx * vty;  // Eq. 8
   const float d = (float)L.d;

@@ -2,11 +2,10 @@
 // "gradient-based L-BFGS solver"): dot products of the history with probe
 // vectors, the direction as a linear combination, pair differences and axpy.
 //
-// The history pairs are float32.  Double arithmetic runs at 1/64 of the
-// float rate on this GPU, so the products with the history are float32
-// FMAs; each thread sums at most a few elements, a warp sums its lanes
-// with a fixed float32 butterfly, and everything above the warp (warps of a
-// block, blocks of the grid) is float64 with fixed trees: deterministic.
+// Everything is float64: the history pairs, the products with them (FMAs
+// on doubles) and their sums.  Each thread sums a strided share of the
+// elements, warps reduce with a fixed butterfly and blocks with fixed
+// trees, so every result is deterministic.
 #include "common.cuh"
 
 namespace octmc {
@@ -46,29 +45,27 @@ __global__ void __launch_bounds__(kThreads) hist_dots_kernel(const HistDots D, i
   const int k0 = blockIdx.y * kHistChunk;
   const int kn = min(kHistChunk, D.K - k0);  // <= 0 only in row 0 of an empty history
   const bool first = blockIdx.y == 0;
-  const float* h[kHistChunk];
+  const double* h[kHistChunk];
 #pragma unroll
   for (int k = 0; k < kHistChunk; k++) h[k] = (k < kn) ? D.h[k0 + k] : nullptr;
-  float a0[kHistChunk], a1[kHistChunk];
+  double a0[kHistChunk], a1[kHistChunk];
 #pragma unroll
-  for (int k = 0; k < kHistChunk; k++) a0[k] = a1[k] = 0.f;
-  float qq0 = 0.f;
-  double qq1 = 0.0;
+  for (int k = 0; k < kHistChunk; k++) a0[k] = a1[k] = 0.0;
+  double qq0 = 0.0, qq1 = 0.0;
   unsigned long long mx = 0ull;
   for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < n; e += (int64_t)G * kThreads) {
-    const float v0 = D.q0 ? D.q0[e] : 0.f;
+    const double v0 = D.q0 ? D.q0[e] : 0.0;
     const double g = D.q1 ? D.q1[e] : 0.0;
-    const float v1 = (float)g;
 #pragma unroll
     for (int k = 0; k < kHistChunk; k++) {
       if (k < kn) {
-        const float hv = h[k][e];
-        a0[k] = fmaf(hv, v0, a0[k]);
-        a1[k] = fmaf(hv, v1, a1[k]);
+        const double hv = h[k][e];
+        a0[k] = fma(hv, v0, a0[k]);
+        a1[k] = fma(hv, g, a1[k]);
       }
     }
     if (first) {
-      qq0 = fmaf(v0, v0, qq0);
+      qq0 = fma(v0, v0, qq0);
       qq1 = fma(g, g, qq1);
       mx = max(mx, abs_bits(g));
     }
@@ -77,7 +74,7 @@ __global__ void __launch_bounds__(kThreads) hist_dots_kernel(const HistDots D, i
 #pragma unroll
   for (int k = 0; k < kHistChunk; k++) {
     if (k < kn) {
-      float u0 = a0[k], u1 = a1[k];
+      double u0 = a0[k], u1 = a1[k];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         u0 += __shfl_xor_sync(0xffffffffu, u0, o);
@@ -146,32 +143,25 @@ __global__ void __launch_bounds__(kThreads) hist_dots_kernel(const HistDots D, i
   }
 }
 
-// out = cg g + sum_k c_k h_k: the history sum in float32 (fixed order),
-// the g term and the final add in float64.
+// out = cg g + sum_k c_k h_k in float64, the terms added in a fixed order.
 __global__ void __launch_bounds__(kThreads) hist_comb_kernel(const HistComb C, int64_t n, double* __restrict__ out) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
-    float s = 0.f;
+    double s = 0.0;
 #pragma unroll 8
-    for (int k = 0; k < C.K; k++) s = fmaf(C.c[k], C.h[k][e], s);
-    out[e] = fma(C.cg, C.g[e], (double)s);
+    for (int k = 0; k < C.K; k++) s = fma(C.c[k], C.h[k][e], s);
+    out[e] = fma(C.cg, C.g[e], s);
   }
 }
 
 __global__ void sub2_kernel(const double* __restrict__ x1, const double* __restrict__ x0,
                             const double* __restrict__ g1, const double* __restrict__ g0,
-                            float* __restrict__ s, float* __restrict__ y, int64_t n) {
+                            double* __restrict__ s, double* __restrict__ y, int64_t n) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
-    s[e] = (float)(x1[e] - x0[e]);
-    y[e] = (float)(g1[e] - g0[e]);
+    s[e] = x1[e] - x0[e];
+    y[e] = g1[e] - g0[e];
   }
-}
-
-__global__ void to_f32_kernel(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x)
-    out[e] = (float)in[e];
 }
 
 __global__ void axpy_kernel(const double* __restrict__ x, double a, const double* __restrict__ d,
@@ -190,9 +180,8 @@ inline unsigned grid_for(int64_t n) {
 
 }  // namespace
 
-// At least kPerThread elements per thread: each thread's float32 sums
-// stay short and every block ends in butterflies, so short vectors get few
-// blocks.
+// At least kPerThread elements per thread: every block ends in butterflies,
+// so short vectors get few blocks.
 int hist_dots_blocks(int64_t n) {
   int64_t b = (n + (int64_t)kThreads * kPerThread - 1) / ((int64_t)kThreads * kPerThread);
   if (b < 1) b = 1;
@@ -216,13 +205,8 @@ cudaError_t launch_hist_comb(const HistComb& hc, int64_t n, double* out, cudaStr
 }
 
 cudaError_t launch_sub2(const double* x1, const double* x0, const double* g1, const double* g0,
-                        float* s_out, float* y_out, int64_t n, cudaStream_t st) {
+                        double* s_out, double* y_out, int64_t n, cudaStream_t st) {
   sub2_kernel<<<grid_for(n), kThreads, 0, st>>>(x1, x0, g1, g0, s_out, y_out, n);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_to_f32(const double* in, float* out, int64_t n, cudaStream_t st) {
-  to_f32_kernel<<<grid_for(n), kThreads, 0, st>>>(in, out, n);
   return cudaGetLastError();
 }
 

@@ -95,10 +95,9 @@ __global__ void weights_kernel(LevelDev L, const double* __restrict__ disp, floa
         a[V] = s;
         const float* vv = V == 0 ? L.vx : L.vy;
         if (vv) {
-          float v = 0.0f;
-          for (int q = 0; q < 4; q++)
-            v = fmaf(V == 0 ? wyv[q] : wxv[q], vv[V == 0 ? clampi(by - 1 + q, h) : clampi(bx - 1 + q, w)], v);
-          va[V] = v;
+          float dv;
+          if (V == 0) validity_hermite(vv, h, by, ty, &va[V], &dv);
+          else validity_hermite(vv, w, bx, tx, &va[V], &dv);
         }
       }
       const float a0 = fmaxf(0.0f, c0 * va[0]), a1 = fmaxf(0.0f, c1 * va[1]);

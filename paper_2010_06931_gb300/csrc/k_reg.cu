@@ -13,9 +13,11 @@
 //                mu sum_c S_c^2.
 //
 // Per-element arithmetic is float (double arithmetic is 1/64 of the float
-// rate on this GPU, with a long latency); each thread's float partials are
-// widened exactly and every sum across threads and blocks is a float64 tree
-// with a fixed shape.  The grid is fixed for a given size and the "last block
+// rate on this GPU, with a long latency) except for the few float64
+// operations that fix the precision: displacement differences (formed in
+// float64, rounded once), the mean-term sums and the line-search product
+// grad . dir.  Each thread's float partials are widened exactly and every sum
+// across threads and blocks is a float64 tree with a fixed shape.  The grid is fixed for a given size and the "last block
 // finishes" pattern adds the block partials: no waits, no float atomics,
 // bitwise reproducible.
 #include "common.cuh"
@@ -77,12 +79,13 @@ __device__ void sum_partials(const double* partials, int nblocks, double (&v)[N]
 // Block blk of nblk blocks working on one problem's mean-term sums.
 __device__ void msum_body(const double* __restrict__ disp, int64_t plane, EvalResult* res, double* partials,
                           unsigned* counter, int blk, int nblk) {
-  float f[3] = {0.f, 0.f, 0.f};
+  // float64 throughout: the sums S_c nearly cancel at a centred field, so
+  // their relative error is that of the inputs' magnitudes (6 adds per A-scan)
+  double v[3] = {0.0, 0.0, 0.0};
   for (int64_t e = (int64_t)blk * kThreads + threadIdx.x; e < plane; e += (int64_t)nblk * kThreads) {
 #pragma unroll
-    for (int c = 0; c < 3; c++) f[c] += narrow_trunc(disp[c * plane + e]) + narrow_trunc(disp[(3 + c) * plane + e]);
+    for (int c = 0; c < 3; c++) v[c] += disp[c * plane + e] + disp[(3 + c) * plane + e];
   }
-  double v[3] = {widen_exact(f[0]), widen_exact(f[1]), widen_exact(f[2])};
   block_sum<3>(v);
   if (threadIdx.x == 0)
     for (int c = 0; c < 3; c++) partials[blk * 3 + c] = v[c];
@@ -131,7 +134,9 @@ __device__ void reg_body(const RegArgs& A, int blk, int nblk) {
   const LevelDev& L = A.L;
   const int64_t n = (int64_t)L.w * L.h;
   const float inv_eps = (float)(1.0 / A.eps_r);
-  const float alpha = (float)A.alpha;
+  // every pair of the chain carries the level depth d (the per-A-scan scale
+  // of the data term, as the angio term of Eq. 6 does)
+  const float alpha_d = (float)(A.alpha * (double)L.d);
   float two_mu_s[3];
 #pragma unroll
   for (int c = 0; c < 3; c++) two_mu_s[c] = (float)(2.0 * A.mu * A.result->msum[c]);
@@ -141,30 +146,31 @@ __device__ void reg_body(const RegArgs& A, int blk, int nblk) {
   for (int64_t e = (int64_t)blk * kThreads + threadIdx.x; e < 2 * n; e += (int64_t)nblk * kThreads) {
     const int V = e >= n ? 1 : 0;
     const int64_t p = e - V * n;
-    float r = 0.f, gd = 0.f;
+    float r = 0.f;
+    double gd = 0.0;
     const int nx = L.next[V][p], pv = L.prev[V][p];
     const float wn = nx >= 0 ? L.wnext[V][p] : 0.f;
     const float wp = pv >= 0 ? L.wprev[V][p] : 0.f;
 #pragma unroll
     for (int c = 0; c < 3; c++) {
       const double* dc = A.disp + (V * 3 + c) * n;
-      const float x = narrow_trunc(dc[p]);
+      const double x = dc[p];
       float gr = 0.f;
       if (nx >= 0) {  // pair (p, next) is counted at its first sample
         float dl;
-        r = fmaf(wn, huber(narrow_trunc(dc[nx]) - x, inv_eps, &dl), r);
+        r = fmaf(wn, huber((float)(dc[nx] - x), inv_eps, &dl), r);  // float64 difference, rounded once
         gr = fmaf(-wn, dl, gr);
       }
       if (pv >= 0) {
         float dl;
-        huber(x - narrow_trunc(dc[pv]), inv_eps, &dl);
+        huber((float)(x - dc[pv]), inv_eps, &dl);
         gr = fmaf(wp, dl, gr);
       }
       if (A.grad) {
         const int64_t gi = (V * 3 + c) * n + p;
-        const float g = A.gdata[gi] + fmaf(alpha, gr, two_mu_s[c]);
+        const float g = A.gdata[gi] + fmaf(alpha_d, gr, two_mu_s[c]);
         A.grad[gi] = widen_exact(g);
-        if (A.dir) gd = fmaf(g, narrow_trunc(A.dir[gi]), gd);
+        if (A.dir) gd = fma(widen_exact(g), A.dir[gi], gd);  // line-search product in float64
       }
     }
     if (V == 0) {
@@ -172,7 +178,7 @@ __device__ void reg_body(const RegArgs& A, int blk, int nblk) {
       v[1] += widen_exact(A.ang_in[p]);
     }
     v[2] += widen_exact(r);
-    v[3] += widen_exact(gd);
+    v[3] += gd;
   }
   block_sum<4>(v);
   if (threadIdx.x == 0)
@@ -185,9 +191,10 @@ __device__ void reg_body(const RegArgs& A, int blk, int nblk) {
       EvalResult* res = A.result;
       res->terms[0] = v[0];
       res->terms[1] = v[1];
-      res->terms[2] = v[2];
+      const double R = (double)L.d * v[2];
+      res->terms[2] = R;
       res->terms[3] = M;
-      res->terms[4] = A.eta * v[0] + v[1] / A.eta + A.alpha * v[2] + M;
+      res->terms[4] = A.eta * v[0] + v[1] / A.eta + A.alpha * R + M;
       res->terms[5] = A.eta;
       res->gdir = v[3];
       *A.counter = 0u;

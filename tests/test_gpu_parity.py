@@ -1,8 +1,9 @@
 """CUDA path vs the FP64 oracle, through the C ABI (GPU only).
 
-Tolerances (float data term, double reductions): objective 1e-5 relative,
-gradient 1e-4 relative L2 (over the whole field), pyramid bit-exact, the
-L-BFGS direction 1e-5 relative L2 (float32 history pairs), solves 0.05 px RMS.
+Tolerances (float data term, float64 reductions): objective and each of its
+terms 1e-5 relative, gradient 1e-4 relative L2 (over the whole field),
+pyramid bit-exact, the L-BFGS direction 1e-10 relative L2 (float64 history
+and products), converged solves 0.05 px RMS.
 """
 import numpy as np
 import pytest
@@ -39,20 +40,6 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def mean_term_bound(D, mu=None):
-    """Error bound of the library's mean term M = mu sum_c S_c^2, S_c the sum of
-    component c over both scans and all A-scans.  The library forms S_c from
-    float per-thread partials (152 x 256 threads, m = ceil(w h / 38912) A-scans
-    each: 2m displacements truncated to float, 2m float additions) and adds
-    the partials in float64, so |dS_c| <= (1 + m) 2^-23 sum|D_c|."""
-    h, w = D.shape[-2:]
-    mu = 1.0 / (2.0 * w * h) if not mu else mu
-    m = -(-(h * w) // (152 * 256))
-    S, A = D.sum(axis=(0, 2, 3)), np.abs(D).sum(axis=(0, 2, 3))
-    dS = (1 + m) * 2.0 ** -23 * A
-    return mu * float(np.sum(2.0 * np.abs(S) * dS + dS * dS))
-
-
 def compare_eval(p, D, eta=0.8, **kw):
     G = gpu_problem(p, **kw)
     C = cpu_problem(p, **kw)
@@ -64,8 +51,6 @@ def compare_eval(p, D, eta=0.8, **kw):
     assert abs(tg[4] - fc) <= F_TOL * abs(fc), (tg, tc)
     for t in range(4):
         tol = F_TOL * max(abs(tc[t]), 1e-12 * abs(fc))
-        if t == 3:  # M: where the sums S_c nearly cancel, the float partials bound it
-            tol = max(tol, mean_term_bound(np.asarray(D), kw.get("mu")))
         assert abs(tg[t] - tc[t]) <= tol, (t, tg, tc)
     err = rel_l2(g.cpu().numpy(), gc)
     assert err <= G_TOL, err
@@ -222,10 +207,12 @@ def test_lbfgs_direction_parity():
     # <= 8 elements per thread and a 32-lane float32 butterfly before float64 sums:
     # up to ~1e-6 relative error on a product with heavy cancellation, entering
     # the direction only through the small history correction.
+    # float64 pairs and products on both sides; the compact and the two-loop
+    # forms agree in exact arithmetic, so only rounding separates them
     err = rel_l2(d.cpu().numpy(), ref)
     print("lbfgs direction rel L2 %.3e, g'dir rel %.3e" % (err, abs(gtd - g @ ref) / abs(g @ ref)))
-    assert err < 1e-5
-    assert gtd == pytest.approx(float(g @ ref), rel=1e-5)
+    assert err < 1e-10
+    assert gtd == pytest.approx(float(g @ ref), rel=1e-10)
     # a pair with negative curvature is rejected and changes nothing
     assert H.push(cuda(S[0]), cuda(-Y[0])) == 1
     d2, _ = H.direction(cuda(g))
@@ -250,66 +237,78 @@ def test_lbfgs_direction_parity_longest_history():
         assert H.push(cuda(s), cuda(y)) == 0
     d, gtd = H.direction(cuda(g))
     ref = O.lbfgs_direction(S[-32:], Y[-32:], g)
-    assert rel_l2(d.cpu().numpy(), ref) < 1e-5
-    assert gtd == pytest.approx(float(g @ ref), rel=1e-5)
+    assert rel_l2(d.cpu().numpy(), ref) < 1e-10
+    assert gtd == pytest.approx(float(g @ ref), rel=1e-10)
 
 
 def test_solve_level_parity_longest_history(c1):
-    # the solver's speculative pair + gradient products with 2 (m + 1) = 66 history vectors
-    p, cfg = c1
-    G = gpu_problem(p, max_iter=60, lbfgs_m=32, alpha=1.0)
-    C = cpu_problem(p, alpha=1.0)
+    # the solver's speculative pair + gradient products with 2 (m + 1) = 66
+    # history vectors, on the well-posed noise-free pair, both run to the
+    # ftol stopping rule
+    p, cfg = clean_c1()
+    G = gpu_problem(p, lbfgs_m=32, ftol=1e-6)
+    C = cpu_problem(p)
     D = G.zeros(0)
     st = G.solve_level(0, D)
-    Dc, stc = C.solve_level(np.zeros(G.disp_shape(0)), m=32, max_iter=60)
+    Dc, stc = C.solve_level(np.zeros(G.disp_shape(0)), m=32, ftol=1e-6)
     rms = float(np.sqrt(((D.cpu().numpy() - Dc) ** 2).mean()))
-    assert rms <= 0.05, (rms, st, stc)
+    assert st["status"] == 0 and stc["status"] == 0, (st, stc)
+    assert rms <= 0.01, (rms, st, stc)
 
 
-@pytest.mark.parametrize("loss", [1, 0])
-def test_solve_level_parity_c1(c1, loss):
-    # identical algorithm and constants on both sides; compare the solutions
-    p, cfg = c1
-    kw = dict(loss=loss, alpha=1.0)
-    G = gpu_problem(p, max_iter=150, **kw)
-    C = cpu_problem(p, **kw)
-    D = G.zeros(0)
-    st = G.solve_level(0, D)
-    Dc, stc = C.solve_level(np.zeros(G.disp_shape(0)), max_iter=150)
-    Dg = D.cpu().numpy()
+def clean_c1():
+    # the c1 scan pair rendered without noise and saccades: the objective has a
+    # well-determined minimum (two float64 oracle runs whose inputs differ by
+    # 1e-7 relative end 0.001 px apart), so converged solves can be compared tightly
+    return make_config("c1", speckle=False, angio_noise=False, n_saccades=0)
+
+
+@pytest.mark.parametrize("loss", [0, 1])
+def test_solve_full_converged_parity_clean_c1(loss):
+    # the coarse-to-fine solve run to convergence on both sides (status 0 on
+    # every level), identical algorithm and constants; the converged minima
+    # agree far inside the 0.05 px bar, and both recover the known motion
+    p, cfg = clean_c1()
+    T, mask = true_displacement(p, cfg["w"], cfg["h"])
+    G = gpu_problem(p, levels=3, loss=loss, ftol=1e-6)
+    C = cpu_problem(p, loss=loss)
+    Dg, st = G.solve_full()
+    Dc, stc = C.solve_full(3, ftol=1e-6)
+    Dg = Dg.cpu().numpy()
     rms = float(np.sqrt(((Dg - Dc) ** 2).mean()))
-    assert st["eta"] == pytest.approx(stc["eta"], rel=F_TOL)
-    assert rms <= 0.05, (rms, st, stc)
-    # secondary sanity check: both stop at the iteration cap, trajectories differ by rounding
-    assert st["f"] == pytest.approx(stc["f"], rel=5e-3)
+    print("clean c1 converged (loss %d): GPU vs oracle %.4f px, iters %s / %s" %
+          (loss, rms, [s["iters"] for s in st], [s["iters"] for s in stc]))
+    assert [s["status"] for s in st] == [0, 0, 0], st
+    assert [s["status"] for s in stc] == [0, 0, 0], stc
+    assert rms <= 0.01
+    assert st[-1]["f"] == pytest.approx(stc[-1]["f"], rel=1e-5)
+    mask[:, :4] = mask[:, -4:] = False
+    mask[:, :, :4] = mask[:, :, -4:] = False
+    m6 = np.broadcast_to(mask[:, None], T.shape)
+    assert np.sqrt(((Dg - T)[m6] ** 2).mean()) < 0.2
+
+
+def test_solve_full_converged_parity_c1(c1):
+    # the speckled c1 pair (drift, saccades, noise) at the library's default
+    # stopping rule: converged minima within 0.05 px RMS (two float64 oracle runs
+    # whose inputs differ by 1e-7 relative end 0.03 px apart at this ftol)
+    p, cfg = c1
+    G = gpu_problem(p, levels=3)
+    C = cpu_problem(p)
+    Dg, st = G.solve_full()
+    Dc, stc = C.solve_full(3)
+    rms = float(np.sqrt(((Dg.cpu().numpy() - Dc) ** 2).mean()))
+    print("c1 converged: GPU vs oracle %.4f px, iters %s / %s" %
+          (rms, [s["iters"] for s in st], [s["iters"] for s in stc]))
+    assert [s["status"] for s in st] == [0, 0, 0], st
+    assert [s["status"] for s in stc] == [0, 0, 0], stc
+    assert rms <= 0.05
+    assert st[-1]["f"] == pytest.approx(stc[-1]["f"], rel=1e-5)
 
 
 @pytest.fixture(scope="module")
 def c2():
     return make_config("c2")
-
-
-@pytest.mark.parametrize("loss", [0, 1])
-def test_solve_full_parity_clinical_size(c2, loss):
-    # the bench workload (300 x 300 x 512, 3 levels) through the whole
-    # coarse-to-fine path on both sides: same start, same algorithm.  The
-    # solve does not converge within a few hundred iterations, and along
-    # non-converged L-BFGS trajectories any rounding difference grows
-    # geometrically (two float64 runs whose inputs differ by 1e-7 separate
-    # the same way), so the comparison is made at 10 iterations per level.
-    p, cfg = c2
-    kw = dict(alpha=0.1, loss=loss)
-    G = gpu_problem(p, levels=3, max_iter=10, **kw)
-    C = cpu_problem(p, **kw)
-    Dg, st = G.solve_full()
-    Dc, stc = C.solve_full(3, max_iter=10)
-    rms = float(np.sqrt(((Dg.cpu().numpy() - Dc) ** 2).mean()))
-    print("c2 solve_full (loss %d): GPU vs oracle RMS %.4f px" % (loss, rms))
-    # eta of the coarsest level is computed at the same (zero) field
-    assert st[0]["eta"] == pytest.approx(stc[0]["eta"], rel=F_TOL)
-    for a, b in zip(st[1:], stc[1:]):
-        assert a["eta"] == pytest.approx(b["eta"], rel=1e-3)
-    assert rms <= 0.05
 
 
 def test_eval_parity_clinical_size(c2):
