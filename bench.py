@@ -146,8 +146,9 @@ class Clocks:
     def __init__(self, gpu_index):
         self.idx = gpu_index
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_bench_%d.csv" % os.getpid()
+        import tempfile
+        fd, self.path = tempfile.mkstemp(prefix="octmc_clocks_", suffix=".csv")
+        os.close(fd)
 
     def start(self):
         try:

@@ -353,9 +353,11 @@ int octmc_profile_read(octmc_problem *p, double *total_ms, long long *launches);
  * Its scratch is one file-scope device array of 8 MiB (+2.4 KiB), held by
  * every GPU that loads the library until the process exits; it fits grids
  * of at most 262,144 A-scans (w*h); larger grids return
- * OCTMC_ERR_SCRATCH_LIMIT.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  Every call shares the array and
+ * OCTMC_ERR_SCRATCH_LIMIT, and w*h*d/4 must stay below 2^32.  Each call
+ * looks up the array's device address (cudaGetSymbolAddress) for the
+ * current device; the first lookup on a device may load the module there,
+ * so make the first call before any stream capture.  eta, delta0 and eps_h
+ * must be finite.  Every call shares the array and
  * leaves its contents behind: calls that overlap on the GPU (other streams,
  * other threads, same device) race and give wrong results.  Asynchronous on
  * `stream`; errors: INVALID_ARG, SCRATCH_LIMIT, CUDA.

@@ -71,12 +71,13 @@ __device__ __forceinline__ void data_ascan(const DataArgs& A, int64_t p, int lan
             Lv = __fdividef(R * rr, fmaf(qv, is, 1.0f));
           }
           acc[0] += Lv;
-          acc[1] = fmaf(dL, IxX[o], acc[1]);
-          acc[2] = fmaf(dL, IyX[o], acc[2]);
-          acc[3] = fmaf(dL, IzX[o], acc[3]);
-          acc[4] = fmaf(dL, IxY[o], acc[4]);
-          acc[5] = fmaf(dL, IyY[o], acc[5]);
-          acc[6] = fmaf(dL, IzY[o], acc[6]);
+          const float2 d2 = make_float2(dL, dL);
+          float2 t = ffma2(d2, make_float2(IxX[o], IyX[o]), make_float2(acc[1], acc[2]));
+          acc[1] = t.x; acc[2] = t.y;
+          t = ffma2(d2, make_float2(IzX[o], IxY[o]), make_float2(acc[3], acc[4]));
+          acc[3] = t.x; acc[4] = t.y;
+          t = ffma2(d2, make_float2(IyY[o], IzY[o]), make_float2(acc[5], acc[6]));
+          acc[5] = t.x; acc[6] = t.y;
         }
       }
     }

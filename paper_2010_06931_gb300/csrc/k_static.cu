@@ -9,8 +9,9 @@
 // completion counter) lives in one file-scope __device__ array of fixed
 // size, which every GPU that loads the library holds until the process
 // exits.  The array's host-side name is not a device address: its device
-// address is looked up once per device with cudaGetSymbolAddress and passed
-// to the kernels.
+// address is looked up with cudaGetSymbolAddress, for the current device,
+// on every call, and passed to the kernels.
+#include <cmath>
 #include <cstring>
 
 #include "common.cuh"
@@ -21,7 +22,6 @@ namespace {
 constexpr int64_t kStaticMaxAscans = int64_t(1) << 18;  // 262,144 A-scans, e.g. 512 x 512
 constexpr int kFinishBlocks = 152;
 constexpr int kFinishThreads = 256;
-constexpr int kMaxDevices = 64;
 
 struct StaticScratch {
   float str[kStaticMaxAscans];
@@ -33,8 +33,6 @@ struct StaticScratch {
 
 // 8 MiB (+ 2.4 KiB) per device.
 __device__ __align__(256) unsigned char g_static_scratch[sizeof(StaticScratch)];
-
-StaticScratch* g_scratch_ptr[kMaxDevices] = {};
 
 // Widens the float gradient into the caller's float64 buffer and adds the
 // per-A-scan data sums in a fixed order (block trees, last block adds the
@@ -85,20 +83,15 @@ __global__ void __launch_bounds__(kFinishThreads) static_finish_kernel(StaticScr
   }
 }
 
-// Device address of the scratch array for the current device; looked up on
-// the first call made with that device current.
+// Device address of the scratch array for the current device.  It is looked
+// up on every call (cudaGetSymbolAddress allocates nothing and is cheap), so
+// there is no per-device cache to race on between host threads and no stale
+// address after the caller resets the device.
 cudaError_t scratch_for_current_device(StaticScratch** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* ptr = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  if (!g_scratch_ptr[dev]) {
-    void* ptr = nullptr;
-    e = cudaGetSymbolAddress(&ptr, g_static_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = static_cast<StaticScratch*>(ptr);
-  }
-  *out = g_scratch_ptr[dev];
+  *out = static_cast<StaticScratch*>(ptr);
   return cudaSuccess;
 }
 
@@ -114,10 +107,14 @@ extern "C" int octmc_data_term_static(const float* sx, const float* sy, const fl
   if (!sx || !sy || !disp || !sums_out || w < 1 || h < 1 || d < 4 || (d & 3) != 0)
     return OCTMC_ERR_INVALID_ARG;
   if ((ax == nullptr) != (ay == nullptr)) return OCTMC_ERR_INVALID_ARG;
-  if (!(eta > 0) || !(eps_h > 0) || !(delta0 >= 0)) return OCTMC_ERR_INVALID_ARG;
+  if (!(eta > 0) || !(eps_h > 0) || !(delta0 >= 0) || !std::isfinite(eta) || !std::isfinite(eps_h) ||
+      !std::isfinite(delta0))
+    return OCTMC_ERR_INVALID_ARG;
   if (loss != OCTMC_LOSS_PSEUDO_HUBER && loss != OCTMC_LOSS_SSD) return OCTMC_ERR_INVALID_ARG;
   const int64_t n = (int64_t)w * h;
   if (n > kStaticMaxAscans) return OCTMC_ERR_SCRATCH_LIMIT;
+  // the data kernel addresses a volume in 32-bit units of 4 samples
+  if (n * (d / 4) >= (int64_t)1 << 32) return OCTMC_ERR_INVALID_ARG;
   const cudaStream_t st = (cudaStream_t)stream;
   StaticScratch* s = nullptr;
   if (scratch_for_current_device(&s) != cudaSuccess) {

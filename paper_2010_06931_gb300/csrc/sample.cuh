@@ -99,6 +99,36 @@ __device__ __forceinline__ float4 load4<__half>(const void* base, unsigned idx) 
   return make_float4(a.x, a.y, b.x, b.y);
 }
 
+// ---------------------------------------------------------------- packed float pairs
+// Two float lanes per instruction (fma.rn.f32x2): each half is rounded like
+// fmaf, so packed and scalar code give bitwise equal results; the packed
+// form halves the issue slots of the interpolation's multiply-adds.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+
+// Four consecutive depth samples as two packed pairs (k, k+1), (k+2, k+3).
+struct Q4 {
+  float2 lo, hi;
+};
+
+__device__ __forceinline__ Q4 q4(const float4& v) { return {make_float2(v.x, v.y), make_float2(v.z, v.w)}; }
+__device__ __forceinline__ Q4 q4zero() { return {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
+
+// acc += w * s on all four samples (w broadcast to both halves)
+__device__ __forceinline__ void qfma(Q4& acc, float2 w, const Q4& s) {
+  acc.lo = ffma2(w, s.lo, acc.lo);
+  acc.hi = ffma2(w, s.hi, acc.hi);
+}
+
+__device__ __forceinline__ float4 f4(const Q4& q) { return make_float4(q.lo.x, q.lo.y, q.hi.x, q.hi.y); }
+
 __device__ __forceinline__ void fma4(float4& acc, float w, const float4& s) {
   acc.x = fmaf(w, s.x, acc.x);
   acc.y = fmaf(w, s.y, acc.y);
@@ -146,6 +176,30 @@ __device__ __forceinline__ void axial(const float4& T, const float4& Tx, const f
     ex[9] = __shfl_down_sync(kFull, Tx.x, 2);
     ey[9] = __shfl_down_sync(kFull, Ty.x, 2);
   }
+#ifndef OCTMC_AXIAL_PACKED
+#define OCTMC_AXIAL_PACKED 1
+#endif
+#if OCTMC_AXIAL_PACKED
+  // outputs in packed pairs (o, o + 1); each half adds its 4 taps in the
+  // scalar order
+#pragma unroll
+  for (int o = 0; o < 4; o += 2) {
+    float2 a = make_float2(0.f, 0.f), az = a, ax = a, ay = a;
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      const float2 w = make_float2(wz[c], wz[c]), dw = make_float2(dwz[c], dwz[c]);
+      const float2 ev = make_float2(e[R + o + c], e[R + o + 1 + c]);
+      a = ffma2(w, ev, a);
+      az = ffma2(dw, ev, az);
+      ax = ffma2(w, make_float2(ex[R + o + c], ex[R + o + 1 + c]), ax);
+      ay = ffma2(w, make_float2(ey[R + o + c], ey[R + o + 1 + c]), ay);
+    }
+    I[o] = a.x; I[o + 1] = a.y;
+    Iz[o] = az.x; Iz[o + 1] = az.y;
+    Ix[o] = ax.x; Ix[o + 1] = ax.y;
+    Iy[o] = ay.x; Iy[o + 1] = ay.y;
+  }
+#else
 #pragma unroll
   for (int o = 0; o < 4; o++) {
     float a = 0.f, az = 0.f, ax = 0.f, ay = 0.f;
@@ -158,6 +212,7 @@ __device__ __forceinline__ void axial(const float4& T, const float4& Tx, const f
     }
     I[o] = a; Iz[o] = az; Ix[o] = ax; Iy[o] = ay;
   }
+#endif
 }
 
 // Interpolated values (and their displacement derivatives) of one volume
@@ -167,20 +222,23 @@ __device__ __forceinline__ void sample_block(const Vol& V, int kb, int lane, int
                                              float Iz[4], float Ix[4], float Iy[4]) {
   const int qk = kb + 4 * V.q + 4 * (lane - 1);  // first input depth of the lane's group
   const unsigned qc = (unsigned)(min(max(qk, 0), dp - 4) >> 2);
-  float4 T = bcast(0.f), Tx = bcast(0.f), Ty = bcast(0.f);
+  // transverse 4 x 4 interpolation of the group and its x / y derivatives,
+  // in packed pairs along depth (same operations and order as scalar FMAs)
+  Q4 Tq = q4zero(), Txq = q4zero(), Tyq = q4zero();
 #pragma unroll
   for (int b = 0; b < 4; b++) {
-    float4 U = bcast(0.f), Ux = bcast(0.f);
+    Q4 U = q4zero(), Ux = q4zero();
 #pragma unroll
     for (int a = 0; a < 4; a++) {
-      const float4 s = load4<S>(V.base, V.roff[b] + V.coff[a] + qc);
-      fma4(U, V.wx[a], s);
-      fma4(Ux, V.dwx[a], s);
+      const Q4 s = q4(load4<S>(V.base, V.roff[b] + V.coff[a] + qc));
+      qfma(U, make_float2(V.wx[a], V.wx[a]), s);
+      qfma(Ux, make_float2(V.dwx[a], V.dwx[a]), s);
     }
-    fma4(T, V.wy[b], U);
-    fma4(Tx, V.wy[b], Ux);
-    fma4(Ty, V.dwy[b], U);
+    qfma(Tq, make_float2(V.wy[b], V.wy[b]), U);
+    qfma(Txq, make_float2(V.wy[b], V.wy[b]), Ux);
+    qfma(Tyq, make_float2(V.dwy[b], V.dwy[b]), U);
   }
+  float4 T = f4(Tq), Tx = f4(Txq), Ty = f4(Tyq);
   // groups entirely before sample 0 / after the last sample hold the edge value
   if (qk < 0) {
     T = bcast(T.x); Tx = bcast(Tx.x); Ty = bcast(Ty.x);

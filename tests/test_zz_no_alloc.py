@@ -68,3 +68,13 @@ def test_static_entry_point_rejects_oversized_grids():
     rc = lib.octmc_data_term_static(ptr, ptr, None, None, None, None, 4, 4, 6, ptr, 1.0, 0.5, 1e-3, 0,
                                     None, ptr, None)
     assert rc == -1  # depth must be a multiple of 4
+    # 512 x 512 A-scans of 65536 samples: 2^32 groups of 4 samples, beyond the
+    # kernel's 32-bit addressing; rejected before any launch
+    rc = lib.octmc_data_term_static(ptr, ptr, None, None, None, None, 512, 512, 65536, ptr, 1.0, 0.5, 1e-3, 0,
+                                    None, ptr, None)
+    assert rc == -1
+    # non-finite scalars are rejected
+    for eta, delta0, eps_h in ((float("inf"), 0.5, 1e-3), (1.0, float("nan"), 1e-3), (1.0, 0.5, float("inf"))):
+        rc = lib.octmc_data_term_static(ptr, ptr, None, None, None, None, 4, 4, 8, ptr, eta, delta0, eps_h, 0,
+                                        None, ptr, None)
+        assert rc == -1
