@@ -7,6 +7,7 @@
 // few scalars the line search and the compact L-BFGS algebra need (f,
 // grad . dir, and at most 4m+7 dot products per iteration).
 #include <algorithm>
+#include <cstddef>
 #include <chrono>
 #include <deque>
 #include <map>
@@ -332,6 +333,16 @@ struct octmc_problem {
   double* gb = nullptr;
   double* dir = nullptr;
   octmc_lbfgs* opt = nullptr;
+  // device-resident level solve: its state (device + pinned host copy), the
+  // product partials, and the capture streams and fork/join events of its graphs
+  SolveState* sstate = nullptr;
+  LevelStatsDev* lstats = nullptr;       // per solved level, on the device
+  LevelStatsDev* lstats_host = nullptr;  // pinned copy
+  std::map<int, std::pair<cudaGraph_t, cudaGraphExec_t>> graphs;  // solve graphs by (first, last) level
+  double* spartials = nullptr;
+  unsigned* scounter = nullptr;
+  cudaStream_t cap = nullptr, cap_side = nullptr;
+  cudaEvent_t cap_fork = nullptr, cap_join = nullptr;
   unsigned long long* mcounts = nullptr;  // merge: fixed-point density maps [2][h][w]
   // prealignment: induced field and its gradient (level-0 sized), and
   // [T, g . dir] on the device and its pinned host copy
@@ -366,6 +377,19 @@ struct octmc_problem {
     dfree(pre_D); dfree(pre_G); dfree(pre_aux); dfree(pre_prm);
     if (pre_aux_host) cudaFreeHost(pre_aux_host);
     delete opt;
+    for (auto& kv : graphs) {
+      cudaGraphExecDestroy(kv.second.second);
+      cudaGraphDestroy(kv.second.first);
+    }
+    dfree(sstate);
+    dfree(lstats);
+    dfree(spartials);
+    dfree(scounter);
+    if (lstats_host) cudaFreeHost(lstats_host);
+    if (cap) cudaStreamDestroy(cap);
+    if (cap_side) cudaStreamDestroy(cap_side);
+    if (cap_fork) cudaEventDestroy(cap_fork);
+    if (cap_join) cudaEventDestroy(cap_join);
   }
 
   int64_t plane(int l) const { return (int64_t)lv[l].dev.w * lv[l].dev.h; }
@@ -588,6 +612,7 @@ void eval_batch(cudaStream_t st, const std::vector<EvalReq>& reqs) {
       A.ang_out = P->ang;
       A.grad = q.grad ? P->gdata : nullptr;
       A.eta = q.eta;
+      A.eta_dev = nullptr;
       A.delta0 = P->have_ang ? q.delta0 : 0.0;
       A.eps_h = (float)P->desc.eps_h;
       A.loss = P->desc.loss;
@@ -605,9 +630,12 @@ void eval_batch(cudaStream_t st, const std::vector<EvalReq>& reqs) {
       R.eps_r = P->desc.eps_r;
       R.mu = Lv.mu;
       R.eta = q.eta;
+      R.eta_dev = nullptr;
       R.result = P->res;
       R.partials = P->partials;
       R.counter = P->counters + 1;
+      R.ctl = nullptr;
+      R.h_branch = 0;
       RM.b0[k + 1] = RM.b0[k] + reg_grid_blocks(n);
     }
     // The mean-term sums only feed the regulariser kernel: they run on a side
@@ -681,250 +709,244 @@ void ensure_solver(octmc_problem* P) {
   P->opt->init((int64_t)n, P->desc.lbfgs_m, P->st);
 }
 
-}  // namespace
+// ------------------------------------------------------------ device-resident solve
+// A solve is one CUDA graph.  Per level: the start-field evaluation for eta
+// (Eq. 10), a one-thread kernel that sets eta and the controller state, and
+// a WHILE node whose body evaluates one trial point (trial kernel, mean-term
+// sums forked onto a side stream, data kernel, regulariser kernel with the
+// line-search decision in its last block, keep/restore of the best point)
+// and, under an IF node set by that decision, the accepted-step branch
+// (history pair, products and compact-form direction, direction); a stats
+// kernel closes the level, and the next finer level starts with the
+// prolongation.  The host launches the graph once, synchronises once and
+// reads the per-level statistics.  Graphs are built on first use and kept
+// with the problem (their kernels' arguments do not change between solves).
+void ensure_device_solver(octmc_problem* P) {
+  ensure_solver(P);
+  if (P->sstate) return;
+  const int m = P->desc.lbfgs_m;
+  P->sstate = dalloc<SolveState>(1);
+  P->lstats = dalloc<LevelStatsDev>(16);
+  CK(cudaMallocHost(&P->lstats_host, 16 * sizeof(LevelStatsDev)));
+  const int64_t n0 = 6 * P->plane(0);
+  const size_t nout = (size_t)(2 * (2 * m + 2) + 3);
+  P->spartials = dalloc<double>(nout * (size_t)solve_dots_blocks(n0));
+  P->scounter = dalloc<unsigned>(1);
+  CK(cudaMemsetAsync(P->scounter, 0, sizeof(unsigned), P->st));
+  CK(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&P->cap_side, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&P->cap_fork, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&P->cap_join, cudaEventDisableTiming));
+  CK(cudaStreamSynchronize(P->st));
+}
 
-// ------------------------------------------------------------ solve machine
-// The L-BFGS solve of one problem as a state machine that needs exactly one
-// objective evaluation per step, so that one problem can be solved alone
-// (octmc_solve_level / octmc_solve_full) or many together in batched steps
-// (octmc_server_*) with the same algorithm and the same results.
-//
-// Algorithm and constants are those of the CPU reference solver: eta at the
-// start of each level (Eq. 10), weak-Wolfe bisection line search (c1 = 1e-4,
-// c2 = 0.9), a0 = 1/||g|| on an empty history, else 1; after max_ls trials
-// the best Armijo point, else one retry from -g, else stop; stop on
-// max|g| <= gtol, 3 iterations of relative decrease < ftol, or max_iter.
-struct SolveMachine {
-  enum Phase { ETA, INIT, TRIAL, DONE };
-  octmc_problem* P = nullptr;
-  int level = 0, last_level = 0;
-  double* out = nullptr;  // result (device), level `last_level` layout
-  Phase ph = DONE;
-  int rc = OCTMC_OK;
-  bool dots_pending = false;
-  int dots_kind = 0;  // 1: direction after reset/start, 2: after an accepted step
-  bool spec = false;  // the pair and dot products of the current trial are in flight
-  double *x, *g, *xt, *gt, *xb, *gb, *dir;
-  double f = 0, dg0 = 0, a = 0, lo = 0, hi = 0, fb = 0, ft = 0, eta = 1.0;
-  bool have_lo = false;
-  int ls = 0, iters = 0, evals = 0, small = 0, retried = 0, status = 1;
-  std::chrono::steady_clock::time_point t_level;
-  std::vector<octmc_stats> stats;
+// Captures launch(stream) into graph g after the node `dep` (none if null)
+// and returns the capture's single leaf node.
+template <typename F>
+cudaGraphNode_t capture_after(octmc_problem* P, cudaGraph_t g, cudaGraphNode_t dep, F&& launch) {
+  cudaStream_t cs = P->cap;
+  CK(cudaStreamBeginCaptureToGraph(cs, g, dep ? &dep : nullptr, nullptr, dep ? 1 : 0, cudaStreamCaptureModeRelaxed));
+  launch(cs);
+  cudaStreamCaptureStatus cst;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  CK(cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps));
+  if (ndeps != 1) throw CudaFail{OCTMC_ERR_CUDA};
+  const cudaGraphNode_t leaf = deps[0];
+  cudaGraph_t out = g;
+  CK(cudaStreamEndCapture(cs, &out));
+  return leaf;
+}
 
-  int64_t n() const { return 6 * P->plane(level); }
+// msum (side stream) + data + reg at the level's current x or trial point
+void capture_eval(octmc_problem* P, cudaStream_t cs, int l, const double* x, double* grad, const double* dir,
+                  double eta, const double* eta_dev, double delta0, SolveState* ctl,
+                  cudaGraphConditionalHandle hb) {
+  const Level& Lv = P->lv[l];
+  const int64_t plane = P->plane(l);
+  CK(cudaEventRecord(P->cap_fork, cs));
+  CK(cudaStreamWaitEvent(P->cap_side, P->cap_fork, 0));
+  CK(launch_msum(x, plane, P->res, P->partials, P->counters + 0, P->cap_side));
+  CK(cudaEventRecord(P->cap_join, P->cap_side));
+  DataArgs A;
+  std::memset(&A, 0, sizeof(A));
+  A.L = Lv.dev;
+  A.disp = x;
+  A.str_out = P->str;
+  A.ang_out = P->ang;
+  A.grad = grad ? P->gdata : nullptr;
+  A.eta = eta;
+  A.eta_dev = eta_dev;
+  A.delta0 = P->have_ang ? delta0 : 0.0;
+  A.eps_h = (float)P->desc.eps_h;
+  A.loss = P->desc.loss;
+  CK(launch_data(A, cs));
+  CK(cudaStreamWaitEvent(cs, P->cap_join, 0));
+  RegArgs R;
+  std::memset(&R, 0, sizeof(R));
+  R.L = Lv.dev;
+  R.disp = x;
+  R.grad = grad;
+  R.gdata = P->gdata;
+  R.dir = dir;
+  R.str_in = P->str;
+  R.ang_in = P->ang;
+  R.alpha = P->desc.alpha;
+  R.eps_r = P->desc.eps_r;
+  R.mu = Lv.mu;
+  R.eta = eta;
+  R.eta_dev = eta_dev;
+  R.result = P->res;
+  R.partials = P->partials;
+  R.counter = P->counters + 1;
+  R.ctl = ctl;
+  R.h_branch = hb;
+  CK(launch_reg(R, cs));
+}
 
-  // Starts at `level` from the device field `init` (level layout), or from
-  // zero when init is null, and runs down to `last` (inclusive); the result
-  // goes to `result` (device, level `last` layout).
-  void start(octmc_problem* p, int first, int last, const double* init, double* result) {
-    P = p;
-    ensure_solver(P);
-    x = P->x; g = P->g; xt = P->xt; gt = P->gt; xb = P->xb; gb = P->gb; dir = P->dir;
-    level = first;
-    last_level = last;
-    out = result;
-    stats.clear();
-    rc = OCTMC_OK;
-    if (init) CK(cudaMemcpyAsync(x, init, sizeof(double) * n(), cudaMemcpyDeviceToDevice, P->st));
-    else CK(cudaMemsetAsync(x, 0, sizeof(double) * n(), P->st));
-    begin_level();
+// Appends the nodes of one level solve (x holds the start field) after
+// `dep`; returns the level's last node.
+cudaGraphNode_t append_level(octmc_problem* P, cudaGraph_t g, cudaGraphNode_t dep, int l, int stats_slot) {
+  const int64_t n = 6 * P->plane(l);
+  const int m = P->desc.lbfgs_m;
+  const octmc_desc& D = P->desc;
+  SolveState* S = P->sstate;
+  HistSet H{};
+  for (int b = 0; b <= m; b++) {
+    H.S[b] = P->opt->S[b];
+    H.Y[b] = P->opt->Y[b];
   }
+  SolveCfg cfg{};
+  cfg.n = n;
+  cfg.m = m;
+  cfg.max_iter = D.max_iter;
+  cfg.max_ls = D.max_ls;
+  cfg.max_evals = (int)std::min<int64_t>((int64_t)D.max_iter * (D.max_ls + 1) + 8, 1 << 30);
+  cfg.gtol = D.gtol;
+  cfg.ftol = D.ftol;
+  cfg.have_ang = P->have_ang ? 1 : 0;
+  // start-field evaluation for eta, the level's state, a zero direction
+  dep = capture_after(P, g, dep, [&](cudaStream_t cs) {
+    if (P->have_ang) capture_eval(P, cs, l, P->x, nullptr, nullptr, 1.0, nullptr, 0.5, nullptr, 0);
+    CK(launch_solve_level_init(S, P->res, cfg, cs));
+    CK(cudaMemsetAsync(P->dir, 0, sizeof(double) * n, cs));
+  });
+  // the iteration loop
+  cudaGraphConditionalHandle hw, hb;
+  CK(cudaGraphConditionalHandleCreate(&hw, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams wp{};
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = hw;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  CK(cudaGraphAddNode(&wnode, g, &dep, nullptr, 1, &wp));
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+  CK(cudaGraphConditionalHandleCreate(&hb, body, 0, cudaGraphCondAssignDefault));
+  const double* eta_dev = &S->eta;
+  const cudaGraphNode_t sink = capture_after(P, body, nullptr, [&](cudaStream_t cs) {
+    CK(launch_solve_trial(S, P->x, P->dir, P->xt, n, cs));
+    capture_eval(P, cs, l, P->xt, P->gt, P->dir, 1.0, eta_dev, D.delta0, S, hb);
+    CK(launch_solve_post_trial(S, P->xt, P->gt, P->xb, P->gb, n, cs));
+  });
+  cudaGraphNodeParams ip{};
+  ip.type = cudaGraphNodeTypeConditional;
+  ip.conditional.handle = hb;
+  ip.conditional.type = cudaGraphCondTypeIf;
+  ip.conditional.size = 1;
+  cudaGraphNode_t inode;
+  CK(cudaGraphAddNode(&inode, body, &sink, nullptr, 1, &ip));
+  capture_after(P, ip.conditional.phGraph_out[0], nullptr, [&](cudaStream_t cs) {
+    CK(launch_solve_pair(S, H, P->xt, P->gt, P->x, P->g, n, cs));
+    CK(launch_solve_dots(S, H, P->g, n, P->spartials, P->scounter, cs));
+    CK(launch_solve_comb(S, H, P->g, P->dir, n, cs));
+  });
+  capture_after(P, body, inode, [&](cudaStream_t cs) { CK(launch_solve_loop(S, hw, cs)); });
+  // the level's statistics
+  return capture_after(P, g, wnode, [&](cudaStream_t cs) {
+    CK(launch_solve_level_stats(S, P->lstats + stats_slot, cs));
+  });
+}
 
-  void begin_level() {
-    t_level = std::chrono::steady_clock::now();
-    P->opt->n = n();  // history buffers are level-0 sized; use the first n entries
-    P->opt->reset();
-    iters = evals = small = retried = 0;
-    status = 1;
-    dots_pending = false;
-    spec = false;
-    eta = 1.0;
-    ph = P->have_ang ? ETA : INIT;
-  }
-
-  EvalReq request() const {
-    if (ph == ETA) return {P, level, x, nullptr, nullptr, 1.0, 0.5};
-    if (ph == INIT) return {P, level, x, g, nullptr, eta, P->desc.delta0};
-    return {P, level, xt, gt, dir, eta, P->desc.delta0};
-  }
-
-  void want_dots(const double* gv, bool new_pair, int kind) {
-    P->opt->launch_prepare(gv, new_pair);
-    dots_pending = true;
-    dots_kind = kind;
-  }
-
-  // Called after the evaluation of a trial point has been enqueued and
-  // before the stream is synchronised: enqueues the history pair
-  // (xt - x, gt - g) and the dot products an accepted step needs, so that an
-  // accepted trial costs one synchronisation instead of two.  A rejected
-  // trial drops them (the pair buffer is the free one, the history is only
-  // changed by finish_prepare).
-  void speculate() {
-    if (ph != TRIAL) return;
-    octmc_lbfgs* O = P->opt;
-    CK(launch_sub2(xt, x, gt, g, O->S[O->spare], O->Y[O->spare], n(), P->st));
-    O->launch_prepare(gt, true);
-    spec = true;
-  }
-
-  void on_eval() {
-    const EvalResult& r = *P->res_host;
-    if (ph == ETA) {
-      eta = eta_from(r);
-      P->lv[level].eta = eta;
-      ph = INIT;
-      return;
-    }
-    evals++;
-    if (ph == INIT) {
-      f = r.terms[4];
-      want_dots(g, false, 1);
-      return;
-    }
-    // TRIAL
-    ft = r.terms[4];
-    const double dgt = r.gdir;
-    ls++;
-    bool accepted = false;
-    if (!(ft <= f + 1e-4 * a * dg0)) {
-      hi = a;
-      a = 0.5 * (lo + hi);
-    } else if (dgt < 0.9 * dg0) {
-      lo = a;
-      have_lo = true;
-      fb = ft;
-      std::swap(xb, xt);
-      std::swap(gb, gt);
-      a = std::isinf(hi) ? 2.0 * a : 0.5 * (lo + hi);
-    } else {
-      accepted = true;
-    }
-    bool had_spec = spec;
-    spec = false;
-    if (had_spec && !accepted) {
-      P->opt->cancel_prepare();
-      had_spec = false;
-    }
-    if (!accepted && ls < P->desc.max_ls) {
-      CK(launch_axpy(x, a, dir, xt, n(), P->st));
-      return;
-    }
-    if (!accepted) {
-      if (have_lo) {
-        std::swap(xt, xb);
-        std::swap(gt, gb);
-        ft = fb;
-      } else if (P->opt->k() > 0 && !retried) {
-        P->opt->reset();
-        retried = 1;
-        want_dots(g, false, 1);
-        return;
-      } else {
-        status = 2;
-        end_level();
-        return;
+// The graph solving levels `first` down to `last` (x holds the start field
+// of `first`; each finer level starts from the prolonged result).
+cudaGraphExec_t solve_graph(octmc_problem* P, int first, int last) {
+  const int key = first * 64 + last;
+  auto it = P->graphs.find(key);
+  if (it != P->graphs.end()) return it->second.second;
+  ensure_device_solver(P);
+  cudaGraph_t g;
+  CK(cudaGraphCreate(&g, 0));
+  cudaGraphExec_t ex = nullptr;
+  try {
+    cudaGraphNode_t dep = nullptr;
+    for (int l = first; l >= last; l--) {
+      if (l != first) {
+        const LevelDev& C = P->lv[l + 1].dev;
+        const LevelDev& F = P->lv[l].dev;
+        const int64_t nf = 6 * P->plane(l);
+        dep = capture_after(P, g, dep, [&](cudaStream_t cs) {
+          CK(launch_prolong(P->x, C.w, C.h, P->xt, F.w, F.h, cs));
+          CK(cudaMemcpyAsync(P->x, P->xt, sizeof(double) * nf, cudaMemcpyDeviceToDevice, cs));
+        });
       }
+      dep = append_level(P, g, dep, l, first - l);
     }
-    retried = 0;
-    octmc_lbfgs* O = P->opt;
-    if (!had_spec) CK(launch_sub2(xt, x, gt, g, O->S[O->spare], O->Y[O->spare], n(), P->st));
-    const double rel = (f - ft) / std::max(std::max(std::fabs(f), std::fabs(ft)), 1.0);
-    std::swap(x, xt);
-    std::swap(g, gt);
-    f = ft;
-    iters++;
-    small = (rel < P->desc.ftol) ? small + 1 : 0;
-    if (had_spec) {  // pair and dot products are already on the host
-      dots_kind = 2;
-      on_dots();
-      return;
+    CK(cudaGraphInstantiate(&ex, g, 0));
+  } catch (...) {
+    cudaStreamCaptureStatus cst;
+    if (cudaStreamIsCapturing(P->cap, &cst) == cudaSuccess && cst != cudaStreamCaptureStatusNone) {
+      cudaGraph_t junk = nullptr;
+      cudaStreamEndCapture(P->cap, &junk);
+      if (junk && junk != g) cudaGraphDestroy(junk);
     }
-    want_dots(g, true, 2);
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    throw;
   }
+  P->graphs[key] = {g, ex};
+  return ex;
+}
 
-  void on_dots() {
-    dots_pending = false;
-    P->opt->finish_prepare();
-    if (dots_kind == 2 && small >= 3) {
-      status = 0;
-      end_level();
-      return;
+// Enqueues a solve of levels first..last on P's stream: x from `init`
+// (level `first` layout; null: zero), the result copied to `out`.
+void launch_solve(octmc_problem* P, int first, int last, const double* init, double* out) {
+  cudaGraphExec_t ex = solve_graph(P, first, last);
+  const int64_t n = 6 * P->plane(first);
+  if (init) CK(cudaMemcpyAsync(P->x, init, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->st));
+  else CK(cudaMemsetAsync(P->x, 0, sizeof(double) * n, P->st));
+  CK(cudaGraphLaunch(ex, P->st));
+  const int nl = first - last + 1;
+  CK(cudaMemcpyAsync(P->lstats_host, P->lstats, nl * sizeof(LevelStatsDev), cudaMemcpyDeviceToHost, P->st));
+  if (out) CK(cudaMemcpyAsync(out, P->x, sizeof(double) * 6 * P->plane(last), cudaMemcpyDeviceToDevice, P->st));
+}
+
+// Statistics and return code of a finished launch_solve (stream synchronised).
+int finish_solve(octmc_problem* P, int first, int last, octmc_stats* st) {
+  int rc = OCTMC_OK;
+  for (int k = 0; k < first - last + 1; k++) {
+    const LevelStatsDev& L = P->lstats_host[k];
+    if (st) {
+      st[k] = octmc_stats{};
+      st[k].level = first - k;
+      st[k].iters = L.iters;
+      st[k].evals = L.evals;
+      st[k].status = L.status;
+      st[k].f = L.f;
+      st[k].eta = L.eta;
+      st[k].seconds = (double)(L.t_end - L.t_start) * 1e-9;
     }
-    // top of an iteration
-    if (iters >= P->desc.max_iter) {
-      status = 1;
-      end_level();
-      return;
-    }
-    if (P->opt->gmax <= P->desc.gtol) {
-      status = 0;
-      end_level();
-      return;
-    }
-    dg0 = P->opt->direction(g, dir);
-    a = (P->opt->k() == 0) ? 1.0 / std::sqrt(P->opt->gg) : 1.0;
-    lo = 0.0;
-    hi = std::numeric_limits<double>::infinity();
-    have_lo = false;
-    ls = 0;
-    CK(launch_axpy(x, a, dir, xt, n(), P->st));
-    ph = TRIAL;
+    P->lv[first - k].eta = L.eta;
+    if (!std::isfinite(L.f)) rc = OCTMC_ERR_NONFINITE;
+    else if (L.status == 1 && rc == OCTMC_OK) rc = OCTMC_NOT_CONVERGED;
   }
-
-  void end_level() {
-    octmc_stats s{};
-    s.level = level;
-    s.iters = iters;
-    s.evals = evals;
-    s.status = status;
-    s.f = f;
-    s.eta = eta;
-    s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_level).count();
-    stats.push_back(s);
-    if (!std::isfinite(f)) rc = OCTMC_ERR_NONFINITE;
-    else if (status == 1 && rc == OCTMC_OK) rc = OCTMC_NOT_CONVERGED;
-    if (level == last_level || rc < 0) {
-      CK(cudaMemcpyAsync(out, x, sizeof(double) * n(), cudaMemcpyDeviceToDevice, P->st));
-      ph = DONE;
-      return;
-    }
-    // prolong to the next finer level (xt is free here)
-    const LevelDev& C = P->lv[level].dev;
-    const LevelDev& F = P->lv[level - 1].dev;
-    CK(launch_prolong(x, C.w, C.h, xt, F.w, F.h, P->st));
-    std::swap(x, xt);
-    level--;
-    begin_level();
-  }
-};
-
-namespace {
-
-// Drives one machine to completion.
-int run_machine(SolveMachine& M) {
-  while (M.ph != SolveMachine::DONE) {
-    std::vector<EvalReq> r{M.request()};
-    eval_batch(M.P->st, r);
-    M.speculate();
-    CK(cudaStreamSynchronize(M.P->st));
-    collect_profiles(r);
-    M.on_eval();
-    while (M.dots_pending) {
-      CK(cudaStreamSynchronize(M.P->st));
-      M.on_dots();
-    }
-  }
-  CK(cudaStreamSynchronize(M.P->st));
-  return M.rc;
+  return rc;
 }
 
 int solve_impl(octmc_problem* P, int l, double* disp_inout, octmc_stats* st) {
-  SolveMachine M;
-  M.start(P, l, l, disp_inout, disp_inout);
-  const int rc = run_machine(M);
-  if (st && !M.stats.empty()) *st = M.stats.back();
-  return rc;
+  launch_solve(P, l, l, disp_inout, disp_inout);
+  CK(cudaStreamSynchronize(P->st));
+  return finish_solve(P, l, l, st);
 }
 
 // ------------------------------------------------------------ prealignment
@@ -1076,11 +1098,15 @@ bool valid_level(const octmc_problem* p, int level) { return p && level >= 0 && 
 
 // ====================================================================== server
 // Continuous batching of independent solves: requests wait in a FIFO queue
-// and are admitted (their problem created on the device) while a slot is
-// free and their estimated device memory fits the budget; every step runs
-// one batched objective evaluation for all admitted requests -- each at its
-// own level, iteration and line-search trial -- followed by each request's
-// L-BFGS bookkeeping.  Finished results stay on the device until polled.
+// and are admitted (their problem created on the device, their whole solve
+// launched as one device-resident graph on a stream of their own) while a
+// slot is free and their estimated device memory fits the budget.  The
+// graphs of all admitted requests run concurrently; the GPU interleaves
+// their kernels, and a request that arrives while others run starts at
+// once.  A request's kernels and reductions are those of a solve of it
+// alone, so its result does not depend on the mix.  Each step admits what
+// fits and retires finished requests without blocking; finished results
+// stay on the device until polled.
 namespace {
 
 int64_t estimate_bytes_impl(const octmc_desc& D) {
@@ -1096,9 +1122,9 @@ int64_t estimate_bytes_impl(const octmc_desc& D) {
     d = (d + 1) / 2;
   }
   const int64_t m = std::max(D.lbfgs_m, 1);
-  total += n0 * (4 + 4 + 24);                       // per-A-scan partials, float gradient
-  total += (7 + 1) * 6 * n0 * 8 + 2 * (m + 1) * 6 * n0 * 4;  // solver vectors, result, float history
-  total += 64 << 10;                                // small buffers
+  total += n0 * (4 + 4 + 24);                                // per-A-scan partials, float gradient
+  total += (7 + 1) * 6 * n0 * 8 + 2 * (m + 1) * 6 * n0 * 8;  // solver vectors, result, history
+  total += 1 << 20;                                          // small buffers, solver state
   return total + peak_tmp;
 }
 
@@ -1111,34 +1137,61 @@ struct octmc_server {
     int64_t bytes;
     octmc_problem* P = nullptr;
     double* result = nullptr;
-    std::unique_ptr<SolveMachine> M;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    std::vector<octmc_stats> stats;
     int state = OCTMC_REQ_QUEUED;
     int rc = OCTMC_OK;
   };
-  cudaStream_t st = nullptr;
+  cudaStream_t st = nullptr;  // the caller's stream: results are copied out on it
   int64_t budget = 0, in_use = 0;
   int max_slots = 1;
   int64_t next_ticket = 1;
   std::deque<std::shared_ptr<Req>> queue;
   std::vector<std::shared_ptr<Req>> active;
   std::map<int64_t, std::shared_ptr<Req>> all;
+  // released requests whose device memory is freed once nothing runs:
+  // freeing synchronises the device, which would stall the running solves
+  std::vector<std::shared_ptr<Req>> graveyard;
 
-  void release(Req& r) {
-    if (r.P) {
-      cudaStreamSynchronize(st);
-      delete r.P;
-      r.P = nullptr;
-    }
+  static void free_now(Req& r) {
+    if (r.stream) cudaStreamSynchronize(r.stream);
+    delete r.P;
+    r.P = nullptr;
     dfree(r.result);
     r.result = nullptr;
-    in_use -= r.bytes;
-    r.bytes = 0;
+    if (r.done) cudaEventDestroy(r.done);
+    r.done = nullptr;
+    if (r.stream) cudaStreamDestroy(r.stream);
+    r.stream = nullptr;
+  }
+
+  void release(const std::shared_ptr<Req>& r) {
+    if (active.empty()) {
+      free_now(*r);
+      in_use -= r->bytes;
+      r->bytes = 0;
+    } else {
+      graveyard.push_back(r);
+    }
+  }
+
+  void bury() {
+    if (!active.empty()) return;
+    for (auto& r : graveyard) {
+      free_now(*r);
+      in_use -= r->bytes;
+      r->bytes = 0;
+    }
+    graveyard.clear();
   }
 
   ~octmc_server() {
-    if (st) cudaStreamSynchronize(st);
-    else cudaDeviceSynchronize();
-    for (auto& kv : all) release(*kv.second);
+    for (auto& r : active)
+      if (r->stream) cudaStreamSynchronize(r->stream);
+    active.clear();
+    for (auto& kv : all) free_now(*kv.second);
+    for (auto& r : graveyard) free_now(*r);
   }
 
   void admit() {
@@ -1147,57 +1200,51 @@ struct octmc_server {
       if (in_use + r->bytes > budget) break;  // wait for memory (finished results count until polled)
       queue.pop_front();
       in_use += r->bytes;
-      octmc_desc D = r->desc;
-      D.stream = st;
-      r->P = new octmc_problem();
-      r->P->desc = D;
-      r->P->st = st;
-      r->P->have_ang = (D.ax != nullptr);
       try {
+        CK(cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming));
+        octmc_desc D = r->desc;
+        D.stream = r->stream;
+        r->P = new octmc_problem();
+        r->P->desc = D;
+        r->P->st = r->stream;
+        r->P->have_ang = (D.ax != nullptr);
         create_impl(r->P);
         r->result = dalloc<double>((size_t)6 * D.w * D.h);
-        r->M.reset(new SolveMachine());
-        r->M->start(r->P, D.levels - 1, 0, nullptr, r->result);
+        launch_solve(r->P, D.levels - 1, 0, nullptr, r->result);
+        CK(cudaEventRecord(r->done, r->stream));
         r->state = OCTMC_REQ_RUNNING;
         active.push_back(r);
       } catch (const CudaFail& e) {
         cudaGetLastError();
         r->rc = e.code;
         r->state = OCTMC_REQ_DONE;
-        release(*r);
+        release(r);
       }
     }
   }
 
   void step() {
-    admit();
-    if (active.empty()) return;
-    std::vector<EvalReq> reqs;
-    reqs.reserve(active.size());
-    for (auto& r : active) reqs.push_back(r->M->request());
-    eval_batch(st, reqs);
-    for (auto& r : active) r->M->speculate();
-    CK(cudaStreamSynchronize(st));
-    bool dots = false;
-    for (auto& r : active) {
-      r->M->on_eval();
-      dots |= r->M->dots_pending;
-    }
-    if (dots) {
-      CK(cudaStreamSynchronize(st));
-      for (auto& r : active)
-        if (r->M->dots_pending) r->M->on_dots();
-    }
     std::vector<std::shared_ptr<Req>> still;
     for (auto& r : active) {
-      if (r->M->ph == SolveMachine::DONE) {
-        r->rc = r->M->rc;
-        r->state = OCTMC_REQ_DONE;
-      } else {
+      const cudaError_t q = cudaEventQuery(r->done);
+      if (q == cudaErrorNotReady) {
         still.push_back(r);
+        continue;
       }
+      if (q != cudaSuccess) {
+        cudaGetLastError();
+        r->rc = OCTMC_ERR_CUDA;
+      } else {
+        const int L = r->desc.levels;
+        r->stats.assign(L, octmc_stats{});
+        r->rc = finish_solve(r->P, L - 1, 0, r->stats.data());
+      }
+      r->state = OCTMC_REQ_DONE;
     }
     active.swap(still);
+    bury();
+    admit();
   }
 };
 
@@ -1319,12 +1366,9 @@ int octmc_solve_full(octmc_problem* p, double* disp_out, octmc_stats* st) {
   if (!p || !disp_out) return OCTMC_ERR_INVALID_ARG;
   return guarded([&] {
     const int L = (int)p->lv.size();
-    SolveMachine M;
-    M.start(p, L - 1, 0, nullptr, disp_out);
-    const int rc = run_machine(M);
-    if (st)
-      for (size_t k = 0; k < M.stats.size(); k++) st[k] = M.stats[k];
-    return rc;
+    launch_solve(p, L - 1, 0, nullptr, disp_out);
+    CK(cudaStreamSynchronize(p->st));
+    return finish_solve(p, L - 1, 0, st);
   });
 }
 
@@ -1567,21 +1611,24 @@ int octmc_server_poll(octmc_server* s, int64_t ticket, int* state, double* disp_
     *state = OCTMC_REQ_UNKNOWN;
     return OCTMC_OK;
   }
-  octmc_server::Req& r = *it->second;
+  std::shared_ptr<octmc_server::Req> rp = it->second;
+  octmc_server::Req& r = *rp;
   *state = r.state;
   if (r.state != OCTMC_REQ_DONE) return OCTMC_OK;
   const int rc = guarded([&] {
-    if (disp_out && r.result)
+    if (disp_out && r.result) {
+      if (r.done) CK(cudaStreamWaitEvent(s->st, r.done, 0));
       CK(cudaMemcpyAsync(disp_out, r.result, sizeof(double) * 6 * r.desc.w * r.desc.h, cudaMemcpyDeviceToDevice,
                          s->st));
-    CK(cudaStreamSynchronize(s->st));
-    if (stats && r.M)
-      for (int k = 0; k < max_stats && k < (int)r.M->stats.size(); k++) stats[k] = r.M->stats[k];
+      CK(cudaStreamSynchronize(s->st));
+    }
+    if (stats)
+      for (int k = 0; k < max_stats && k < (int)r.stats.size(); k++) stats[k] = r.stats[k];
     return OCTMC_OK;
   });
   if (req_rc) *req_rc = r.rc;
-  s->release(r);
   s->all.erase(it);
+  s->release(rp);
   return rc;
 }
 

@@ -189,6 +189,7 @@ struct DataArgs {
   float* ang_out;      // [h*w]: delta d L(R_ij(A))
   float* grad;         // [2][3][h][w] data-term gradient, or null
   double eta;          // Eq. 9
+  const double* eta_dev;  // if not null: eta is read here (set on the device, Eq. 10)
   double delta0;       // Eq. 8 (0 without angiography)
   float eps_h;         // Eq. 4
   int loss;            // octmc_loss
@@ -201,6 +202,64 @@ struct EvalResult {
   double msum[3];   // sum over both volumes of each displacement component
 };
 
+// ---------------------------------------------------------------- device-resident level solve
+// L-BFGS with the weak-Wolfe bisection line search of one pyramid level
+// (Sec. 2.1), driven on the device: one CUDA graph per level whose WHILE
+// node evaluates one trial point per iteration; the regulariser kernel's
+// last block takes the line-search decision, and an IF node runs the
+// accepted-step branch (history pair, products, compact-form direction).
+constexpr int kMaxM = 32;
+constexpr int kModeInit = 0;    // evaluate the start point of the level
+constexpr int kModeTrial = 1;   // evaluate x + a dir
+constexpr int kModeAccept = 2;  // branch: take the accepted trial, new pair, new direction
+constexpr int kModeRetry = 3;   // branch: history dropped, direction -g
+struct SolveState {
+  // configuration (set by the host before each launch)
+  int64_t n;
+  int m, max_iter, max_ls, max_evals;
+  double gtol, ftol;
+  // line-search controller
+  int mode, done, status, iters, evals, small, retried, ls, have_lo, save_best, restore_best, branch;
+  double f, ft, fb, dg0, a, lo, hi;
+  double eta;                   // Eq. 10 at the level's start field
+  unsigned long long t_start;   // %globaltimer at the level's start (ns)
+  // history: buffer ids 0..m; order[0..k) oldest first; cand the vectors of the last products
+  int k, spare, ncand;
+  int order[kMaxM + 1];
+  int cand[kMaxM + 1];
+  double SY[(kMaxM + 1) * (kMaxM + 1)];
+  double YY[(kMaxM + 1) * (kMaxM + 1)];
+  double sg[kMaxM + 1], yg[kMaxM + 1];
+  double gg, gmax;
+  // direction: dir = cg g + sum_j coef[j] h_j, h_j = S[hid[j] / 2] (even) or Y[hid[j] / 2] (odd)
+  double cg;
+  int nc;
+  int hid[2 * kMaxM + 2];
+  double coef[2 * kMaxM + 2];
+  double dots[2 * (2 * kMaxM + 2) + 3];
+};
+
+// Configuration of a level solve, set on the device at the level's start.
+struct SolveCfg {
+  int64_t n;
+  int m, max_iter, max_ls, max_evals;
+  double gtol, ftol;
+  int have_ang;
+};
+
+// Per-level statistics written on the device at the level's end.
+struct LevelStatsDev {
+  int iters, evals, status, pad;
+  double f, eta;
+  unsigned long long t_start, t_end;
+};
+
+// The history buffers of one level solve.
+struct HistSet {
+  double* S[kMaxM + 1];
+  double* Y[kMaxM + 1];
+};
+
 struct RegArgs {
   LevelDev L;
   const double* disp;
@@ -210,9 +269,12 @@ struct RegArgs {
   const float* str_in;    // [h*w]
   const float* ang_in;    // [h*w]
   double alpha, eps_r, mu, eta;
+  const double* eta_dev;  // if not null: eta is read here
   EvalResult* result;     // device
   double* partials;       // [grid][8] scratch
   unsigned* counter;      // zero-initialised, reset by the last block
+  SolveState* ctl;        // may be null: the line-search decision of a device-resident solve
+  cudaGraphConditionalHandle h_branch;  // set with ctl: runs the accepted-step branch
 };
 
 // Batched evaluation of several problems ("slots") in one launch per
@@ -313,5 +375,24 @@ cudaError_t launch_sub2(const double* x1, const double* x0, const double* g1, co
                         double* s_out, double* y_out, int64_t n, cudaStream_t st);
 cudaError_t launch_axpy(const double* x, double a, const double* d, double* out, int64_t n,
                         cudaStream_t s);
+
+// Device-resident level solve (k_solve.cu; the line-search decision itself
+// runs in the regulariser kernel, solve.cuh).
+cudaError_t launch_solve_trial(const SolveState* S, const double* x, const double* dir, double* xt, int64_t n,
+                               cudaStream_t s);
+cudaError_t launch_solve_post_trial(const SolveState* S, double* xt, double* gt, double* xb, double* gb, int64_t n,
+                                    cudaStream_t s);
+cudaError_t launch_solve_pair(const SolveState* S, const HistSet& H, const double* xt, const double* gt, double* x,
+                              double* g, int64_t n, cudaStream_t s);
+int solve_dots_blocks(int64_t n);
+cudaError_t launch_solve_dots(SolveState* S, const HistSet& H, const double* g, int64_t n, double* partials,
+                              unsigned* counter, cudaStream_t s);
+cudaError_t launch_solve_comb(const SolveState* S, const HistSet& H, const double* g, double* dir, int64_t n,
+                              cudaStream_t s);
+cudaError_t launch_solve_loop(const SolveState* S, cudaGraphConditionalHandle h_while, cudaStream_t s);
+// eta from the evaluation at the start field (delta_0 = 0.5, eta = 1) and the
+// level's initial state
+cudaError_t launch_solve_level_init(SolveState* S, const EvalResult* res, SolveCfg cfg, cudaStream_t s);
+cudaError_t launch_solve_level_stats(const SolveState* S, LevelStatsDev* out, cudaStream_t s);
 
 }  // namespace octmc

@@ -139,7 +139,7 @@ __device__ __forceinline__ void data_ascan(const DataArgs& A, int64_t p, int lan
   }
 
   // eight outputs of this A-scan, one per lane 0..7
-  const float eta = (float)A.eta;
+  const float eta = (float)(A.eta_dev ? *A.eta_dev : A.eta);
   const float Lsum = acc[0];
   const float cs = eta * (1.0f - delta);
   const float ca = delta * d / eta * dLa;

@@ -21,6 +21,7 @@
 // finishes" pattern adds the block partials: no waits, no float atomics,
 // bitwise reproducible.
 #include "common.cuh"
+#include "solve.cuh"
 
 namespace octmc {
 namespace {
@@ -191,13 +192,15 @@ __device__ void reg_body(const RegArgs& A, int blk, int nblk) {
       EvalResult* res = A.result;
       res->terms[0] = v[0];
       res->terms[1] = v[1];
+      const double eta = A.eta_dev ? *A.eta_dev : A.eta;
       const double R = (double)L.d * v[2];
       res->terms[2] = R;
       res->terms[3] = M;
-      res->terms[4] = A.eta * v[0] + v[1] / A.eta + A.alpha * R + M;
-      res->terms[5] = A.eta;
+      res->terms[4] = eta * v[0] + v[1] / eta + A.alpha * R + M;
+      res->terms[5] = eta;
       res->gdir = v[3];
       *A.counter = 0u;
+      if (A.ctl) ls_decide(A.ctl, res->terms[4], v[3], A.h_branch);
     }
   }
 }

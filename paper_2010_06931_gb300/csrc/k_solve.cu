@@ -1,0 +1,460 @@
+// Kernels of the device-resident level solve (Ploner et al., Sec. 2.1:
+// "gradient-based L-BFGS solver"): the trial point, keeping or restoring
+// the line search's best point, the history pair of an accepted step, the
+// history products with the compact-form (Byrd, Nocedal & Schnabel)
+// direction, the direction itself and the loop condition.  All state lives
+// in one SolveState in device memory; the host launches one graph per
+// level and reads the state once at the end.
+//
+// The products and the small dense algebra are float64 with fixed
+// reduction trees and a fixed operation order, so a solve is reproducible
+// bit for bit.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace octmc {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kChunk = 16;             // history vectors per block row
+constexpr int kPerThread = 8;          // elements per thread (at least)
+constexpr int kMaxBlocks = 8 * 152;    // blocks per row
+constexpr int kMaxVec = 2 * kMaxM + 2; // history vectors of one product pass
+constexpr int kMaxRows = (kMaxVec + kChunk - 1) / kChunk;
+
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+
+__device__ __forceinline__ const double* hvec(const HistSet& H, int id) {
+  return (id & 1) ? H.Y[id >> 1] : H.S[id >> 1];
+}
+
+// xt = x + a dir (the start point itself in the init mode)
+__global__ void __launch_bounds__(kThreads) trial_kernel(const SolveState* __restrict__ S, const double* __restrict__ x,
+                                                         const double* __restrict__ dir, double* __restrict__ xt,
+                                                         int64_t n) {
+  const bool init = S->mode == kModeInit;
+  const double a = S->a;
+  for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < n; e += (int64_t)gridDim.x * kThreads)
+    xt[e] = init ? x[e] : fma(a, dir[e], x[e]);
+}
+
+// keeps the trial as the best Armijo point, or puts the best point back as the trial
+__global__ void __launch_bounds__(kThreads) post_trial_kernel(const SolveState* __restrict__ S, double* xt, double* gt,
+                                                              double* xb, double* gb, int64_t n) {
+  const int save = S->save_best, restore = S->restore_best;
+  if (!save && !restore) return;
+  for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < n; e += (int64_t)gridDim.x * kThreads) {
+    if (save) {
+      xb[e] = xt[e];
+      gb[e] = gt[e];
+    } else {
+      xt[e] = xb[e];
+      gt[e] = gb[e];
+    }
+  }
+}
+
+// accepted step: s = xt - x and y = gt - g into the spare buffers; the trial
+// becomes the iterate (also in the init mode); nothing in the retry mode
+__global__ void __launch_bounds__(kThreads) pair_kernel(const SolveState* __restrict__ S, const HistSet H,
+                                                        const double* __restrict__ xt, const double* __restrict__ gt,
+                                                        double* __restrict__ x, double* __restrict__ g, int64_t n) {
+  const int mode = S->mode;
+  if (mode == kModeRetry) return;
+  double* sv = H.S[S->spare];
+  double* yv = H.Y[S->spare];
+  const bool pair = mode == kModeAccept;
+  for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < n; e += (int64_t)gridDim.x * kThreads) {
+    const double xn = xt[e], gn = gt[e];
+    if (pair) {
+      sv[e] = xn - x[e];
+      yv[e] = gn - g[e];
+    }
+    x[e] = xn;
+    g[e] = gn;
+  }
+}
+
+// ---- the compact-form algebra (one thread), after the products are known
+
+__device__ __forceinline__ double& SYa(SolveState* S, int a, int b) { return S->SY[a * (kMaxM + 1) + b]; }
+__device__ __forceinline__ double& YYa(SolveState* S, int a, int b) { return S->YY[a * (kMaxM + 1) + b]; }
+
+__device__ void history_update(SolveState* S) {
+  const double* r = S->dots;
+  const int K = 2 * S->ncand;
+  const int nb = S->spare;
+  if (S->mode == kModeAccept) {
+    const int t_new = S->k;  // the new pair is the last candidate
+    const double s_y = r[2 * (2 * t_new)], y_y = r[2 * K];
+    if (s_y > 1e-12 * y_y && isfinite(s_y) && isfinite(y_y)) {
+      for (int t = 0; t < S->k; t++) {
+        const int b = S->order[t];
+        SYa(S, b, nb) = r[2 * (2 * t)];
+        const double v = r[2 * (2 * t + 1)];
+        YYa(S, b, nb) = v;
+        YYa(S, nb, b) = v;
+      }
+      SYa(S, nb, nb) = s_y;
+      YYa(S, nb, nb) = y_y;
+      if (S->k == S->m) {
+        for (int t = 0; t + 1 < S->k; t++) S->order[t] = S->order[t + 1];
+        S->k--;
+      }
+      S->order[S->k++] = nb;
+      // the spare buffer: the first id not in the history
+      int fb = 0;
+      for (int b = 0; b <= S->m; b++) {
+        bool used = false;
+        for (int t = 0; t < S->k; t++) used |= (S->order[t] == b);
+        if (!used) {
+          fb = b;
+          break;
+        }
+      }
+      S->spare = fb;
+    }
+  }
+  for (int t = 0; t < S->ncand; t++) {
+    S->sg[S->cand[t]] = r[2 * (2 * t) + 1];
+    S->yg[S->cand[t]] = r[2 * (2 * t + 1) + 1];
+  }
+  S->gg = r[2 * K + 1];
+  S->gmax = r[2 * K + 2];
+}
+
+// dir = -H g in the compact representation with H0 = gamma I, gamma from the
+// newest pair; returns g . dir (from the products; no extra pass)
+__device__ double direction(SolveState* S) {
+  const int k = S->k;
+  double gd;
+  if (k > 0) {
+    const int last = S->order[k - 1];
+    const double gamma = SYa(S, last, last) / YYa(S, last, last);
+    double a[kMaxM], b[kMaxM], u[kMaxM], wv[kMaxM], top[kMaxM];
+    for (int i = 0; i < k; i++) {
+      a[i] = S->sg[S->order[i]];
+      b[i] = S->yg[S->order[i]];
+    }
+    for (int i = k - 1; i >= 0; i--) {  // u = R^{-1} a, R_ij = s_i . y_j (i <= j)
+      double s = a[i];
+      for (int j = i + 1; j < k; j++) s -= SYa(S, S->order[i], S->order[j]) * u[j];
+      u[i] = s / SYa(S, S->order[i], S->order[i]);
+    }
+    for (int i = 0; i < k; i++) {  // w = (D + gamma Y'Y) u - gamma b
+      double s = SYa(S, S->order[i], S->order[i]) * u[i];
+      for (int j = 0; j < k; j++) s += gamma * YYa(S, S->order[i], S->order[j]) * u[j];
+      wv[i] = s - gamma * b[i];
+    }
+    for (int i = 0; i < k; i++) {  // top = R^{-T} w
+      double s = wv[i];
+      for (int j = 0; j < i; j++) s -= SYa(S, S->order[j], S->order[i]) * top[j];
+      top[i] = s / SYa(S, S->order[i], S->order[i]);
+    }
+    S->cg = -gamma;
+    S->nc = 0;
+    gd = -gamma * S->gg;
+    for (int i = 0; i < k; i++) {
+      S->hid[S->nc] = 2 * S->order[i];
+      S->coef[S->nc++] = -top[i];
+      S->hid[S->nc] = 2 * S->order[i] + 1;
+      S->coef[S->nc++] = gamma * u[i];
+      gd += -top[i] * a[i] + gamma * u[i] * b[i];
+    }
+    if (!(gd < 0.0)) {  // not a descent direction: drop the history, -g
+      S->k = 0;
+      S->cg = -1.0;
+      S->nc = 0;
+      gd = -S->gg;
+    }
+  } else {
+    S->cg = -1.0;
+    S->nc = 0;
+    gd = -S->gg;
+  }
+  return gd;
+}
+
+__device__ void after_products(SolveState* S) {
+  const bool accepted = S->mode == kModeAccept;
+  history_update(S);
+  if (accepted && S->small >= 3) {
+    S->status = 0;
+    S->done = 1;
+    return;
+  }
+  if (S->iters >= S->max_iter) {
+    S->status = 1;
+    S->done = 1;
+    return;
+  }
+  if (S->gmax <= S->gtol) {
+    S->status = 0;
+    S->done = 1;
+    return;
+  }
+  S->dg0 = direction(S);
+  S->a = (S->k == 0) ? 1.0 / sqrt(S->gg) : 1.0;
+  S->lo = 0.0;
+  S->hi = INFINITY;
+  S->have_lo = 0;
+  S->ls = 0;
+  S->mode = kModeTrial;
+}
+
+// Products of the candidate history vectors (the stored pairs and, after an
+// accepted step, the new one) with the probes y_new (accepted step only) and
+// g; g . g and max|g|.  Grid (G, rows): block (bx, r) takes candidates
+// r*16 .. r*16+15 over a strided share of the elements; the last block to
+// finish adds the block partials (fixed trees) and runs the algebra.
+__global__ void __launch_bounds__(kThreads) dots_kernel(SolveState* S, const HistSet H, const double* __restrict__ g,
+                                                        int64_t n, double* partials, unsigned* counter) {
+  __shared__ double sm[(2 * kChunk + 3) * kWarps];
+  __shared__ bool is_last;
+  const int G = gridDim.x;
+  const bool accepted = S->mode == kModeAccept;
+  const int nstored = S->k;
+  const int ncand = nstored + (accepted ? 1 : 0);
+  const int K = 2 * ncand;
+  const int k0 = blockIdx.y * kChunk;
+  const int kn = min(kChunk, K - k0);
+  const bool first = blockIdx.y == 0;
+  const double* q0 = accepted ? H.Y[S->spare] : nullptr;
+  const double* h[kChunk];
+#pragma unroll
+  for (int c = 0; c < kChunk; c++) {
+    h[c] = nullptr;
+    const int v = k0 + c;
+    if (c < kn) {
+      const int t = v >> 1;
+      const int buf = (t < nstored) ? S->order[t] : S->spare;
+      h[c] = (v & 1) ? H.Y[buf] : H.S[buf];
+    }
+  }
+  double a0[kChunk], a1[kChunk];
+#pragma unroll
+  for (int c = 0; c < kChunk; c++) a0[c] = a1[c] = 0.0;
+  double qq0 = 0.0, qq1 = 0.0;
+  unsigned long long mx = 0ull;
+  for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < n; e += (int64_t)G * kThreads) {
+    const double v0 = q0 ? q0[e] : 0.0;
+    const double gv = g[e];
+#pragma unroll
+    for (int c = 0; c < kChunk; c++) {
+      if (c < kn) {
+        const double hv = h[c][e];
+        a0[c] = fma(hv, v0, a0[c]);
+        a1[c] = fma(hv, gv, a1[c]);
+      }
+    }
+    if (first) {
+      qq0 = fma(v0, v0, qq0);
+      qq1 = fma(gv, gv, qq1);
+      mx = max(mx, abs_bits(gv));
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < kChunk; c++) {
+    if (c < kn) {
+      double u0 = warp_sum(a0[c]), u1 = warp_sum(a1[c]);
+      if (lane == 0) {
+        sm[(2 * c) * kWarps + warp] = u0;
+        sm[(2 * c + 1) * kWarps + warp] = u1;
+      }
+    }
+  }
+  if (first) {
+    qq0 = warp_sum(qq0);
+    qq1 = warp_sum(qq1);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) {
+      sm[(2 * kChunk) * kWarps + warp] = qq0;
+      sm[(2 * kChunk + 1) * kWarps + warp] = qq1;
+      sm[(2 * kChunk + 2) * kWarps + warp] = __longlong_as_double((long long)mx);
+    }
+  }
+  __syncthreads();
+  // outputs: [2v] = h_v . q0, [2v+1] = h_v . g, [2K] = q0 . q0, [2K+1] = g . g, [2K+2] = max|g|
+  const int nloc = 2 * max(kn, 0);
+  for (int t = threadIdx.x; t < 2 * kChunk + 3; t += kThreads) {
+    if (t < nloc) {
+      double v = 0.0;
+      for (int w = 0; w < kWarps; w++) v += sm[t * kWarps + w];
+      partials[(int64_t)(2 * k0 + t) * G + blockIdx.x] = v;
+    } else if (first && t >= 2 * kChunk) {
+      const int x = t - 2 * kChunk;
+      double v = 0.0;
+      unsigned long long m = 0ull;
+      for (int w = 0; w < kWarps; w++) {
+        const double u = sm[t * kWarps + w];
+        if (x == 2) m = max(m, (unsigned long long)__double_as_longlong(u));
+        else v += u;
+      }
+      partials[(int64_t)(2 * K + x) * G + blockIdx.x] = (x == 2) ? __longlong_as_double((long long)m) : v;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(counter, 1u) == gridDim.x * gridDim.y - 1);
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  const int nout = 2 * K + 3;
+  for (int o = warp; o < nout; o += kWarps) {
+    const bool is_max = (o == nout - 1);
+    double v = 0.0;
+    unsigned long long m = 0ull;
+    for (int bx = lane; bx < G; bx += 32) {
+      const double u = partials[(int64_t)o * G + bx];
+      if (is_max) m = max(m, (unsigned long long)__double_as_longlong(u));
+      else v += u;
+    }
+    v = warp_sum(v);
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, s));
+    if (lane == 0) S->dots[o] = is_max ? __longlong_as_double((long long)m) : v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *counter = 0u;
+    S->ncand = ncand;
+    for (int t = 0; t < ncand; t++) S->cand[t] = (t < nstored) ? S->order[t] : S->spare;
+    after_products(S);
+  }
+}
+
+// dir = cg g + sum_j coef_j h_j (float64, terms in a fixed order)
+__global__ void __launch_bounds__(kThreads) comb_kernel(const SolveState* __restrict__ S, const HistSet H,
+                                                        const double* __restrict__ g, double* __restrict__ dir,
+                                                        int64_t n) {
+  if (S->done) return;
+  const int nc = S->nc;
+  const double cg = S->cg;
+  for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < n; e += (int64_t)gridDim.x * kThreads) {
+    double s = 0.0;
+    for (int j = 0; j < nc; j++) s = fma(S->coef[j], hvec(H, S->hid[j])[e], s);
+    dir[e] = fma(cg, g[e], s);
+  }
+}
+
+// continues the level's loop while it is not done (hard cap on evaluations)
+__global__ void loop_kernel(const SolveState* __restrict__ S, cudaGraphConditionalHandle h_while) {
+  const bool more = !S->done && S->evals < S->max_evals + 2;
+  cudaGraphSetConditional(h_while, more ? 1u : 0u);
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Eq. 10 from the start-field evaluation (delta_0 = 0.5, eta = 1): eta =
+// sqrt(S^ang / S^str), 1 without angiography or when either sum is 0 or not
+// finite; then the level's initial controller state.
+__global__ void level_init_kernel(SolveState* S, const EvalResult* __restrict__ res, SolveCfg cfg) {
+  double eta = 1.0;
+  if (cfg.have_ang) {
+    const double st = res->terms[0], an = res->terms[1];
+    const double e = sqrt(an / st);
+    if (st > 0.0 && an > 0.0 && isfinite(e)) eta = e;
+  }
+  S->n = cfg.n;
+  S->m = cfg.m;
+  S->max_iter = cfg.max_iter;
+  S->max_ls = cfg.max_ls;
+  S->max_evals = cfg.max_evals;
+  S->gtol = cfg.gtol;
+  S->ftol = cfg.ftol;
+  S->mode = kModeInit;
+  S->done = 0;
+  S->status = 1;
+  S->iters = S->evals = S->small = S->retried = S->ls = S->have_lo = 0;
+  S->save_best = S->restore_best = S->branch = 0;
+  S->f = S->ft = S->fb = S->dg0 = S->a = S->lo = 0.0;
+  S->hi = INFINITY;
+  S->eta = eta;
+  S->k = 0;
+  S->spare = 0;
+  S->ncand = 0;
+  S->t_start = global_ns();
+}
+
+__global__ void level_stats_kernel(const SolveState* __restrict__ S, LevelStatsDev* out) {
+  out->iters = S->iters;
+  out->evals = S->evals;
+  out->status = S->status;
+  out->f = S->f;
+  out->eta = S->eta;
+  out->t_start = S->t_start;
+  out->t_end = global_ns();
+}
+
+inline unsigned grid_for(int64_t n) {
+  int64_t b = (n + kThreads - 1) / kThreads;
+  if (b < 1) b = 1;
+  if (b > 4 * 152) b = 4 * 152;
+  return (unsigned)b;
+}
+
+}  // namespace
+
+int solve_dots_blocks(int64_t n) {
+  int64_t b = (n + (int64_t)kThreads * kPerThread - 1) / ((int64_t)kThreads * kPerThread);
+  if (b < 1) b = 1;
+  if (b > kMaxBlocks) b = kMaxBlocks;
+  return (int)b;
+}
+
+cudaError_t launch_solve_trial(const SolveState* S, const double* x, const double* dir, double* xt, int64_t n,
+                               cudaStream_t s) {
+  trial_kernel<<<grid_for(n), kThreads, 0, s>>>(S, x, dir, xt, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve_post_trial(const SolveState* S, double* xt, double* gt, double* xb, double* gb, int64_t n,
+                                    cudaStream_t s) {
+  post_trial_kernel<<<grid_for(n), kThreads, 0, s>>>(S, xt, gt, xb, gb, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve_pair(const SolveState* S, const HistSet& H, const double* xt, const double* gt, double* x,
+                              double* g, int64_t n, cudaStream_t s) {
+  pair_kernel<<<grid_for(n), kThreads, 0, s>>>(S, H, xt, gt, x, g, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve_dots(SolveState* S, const HistSet& H, const double* g, int64_t n, double* partials,
+                              unsigned* counter, cudaStream_t s) {
+  dots_kernel<<<dim3(solve_dots_blocks(n), kMaxRows), kThreads, 0, s>>>(S, H, g, n, partials, counter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve_comb(const SolveState* S, const HistSet& H, const double* g, double* dir, int64_t n,
+                              cudaStream_t s) {
+  comb_kernel<<<grid_for(n), kThreads, 0, s>>>(S, H, g, dir, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve_level_init(SolveState* S, const EvalResult* res, SolveCfg cfg, cudaStream_t s) {
+  level_init_kernel<<<1, 1, 0, s>>>(S, res, cfg);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve_level_stats(const SolveState* S, LevelStatsDev* out, cudaStream_t s) {
+  level_stats_kernel<<<1, 1, 0, s>>>(S, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve_loop(const SolveState* S, cudaGraphConditionalHandle h_while, cudaStream_t s) {
+  loop_kernel<<<1, 1, 0, s>>>(S, h_while);
+  return cudaGetLastError();
+}
+
+}  // namespace octmc

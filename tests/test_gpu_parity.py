@@ -282,11 +282,13 @@ def test_solve_full_converged_parity_clean_c1(loss):
     assert [s["status"] for s in stc] == [0, 0, 0], stc
     assert rms <= 0.01
     # the GPU's minimum is as deep as the oracle's, both measured by the FP64
-    # objective (the GPU's own f carries the float rounding of residuals that
-    # are near zero at a noise-free minimum, about 4e-5 of f)
+    # objective.  The GPU minimises its float-evaluated objective, whose
+    # rounding at this noise-free minimum (residuals near zero, float
+    # interpolants rounded at 2^-24 of values up to 1 on 2.6e5 voxel pairs) is
+    # about 4e-5 of f, so its minimum may sit that much higher in FP64
     P0 = C.pyramid(1)[0]
     P0.eta = stc[-1]["eta"]
-    assert P0.eval(Dg, grad=False)[0] == pytest.approx(stc[-1]["f"], rel=1e-6)
+    assert P0.eval(Dg, grad=False)[0] == pytest.approx(stc[-1]["f"], rel=1e-4)
     mask[:, :4] = mask[:, -4:] = False
     mask[:, :, :4] = mask[:, :, -4:] = False
     m6 = np.broadcast_to(mask[:, None], T.shape)
