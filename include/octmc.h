@@ -137,6 +137,22 @@ int octmc_eval_objective_grad(octmc_problem *p, int level, const double *disp_de
 int octmc_eval_terms(octmc_problem *p, int level, const double *disp_dev, double *terms_host,
                      double *grad_dev);
 
+/* Objectives (and gradients) of several independent problems evaluated
+ * together, as octmc_eval_objective_grad does for one: one launch per
+ * kernel for all of them (mean-term sums, data term per storage type,
+ * regulariser), each problem with the blocks, partition and reduction order
+ * of an evaluation of it alone, so every result equals the single call's.
+ *   problems[k] (distinct), levels[k], disp_dev[k] (device field of that
+ *   level), grad_dev[k] (device, may be NULL, or grad_dev itself NULL),
+ *   f_host[k] (host, may be NULL) receives f.
+ * Each problem uses its level's stored eta.  The call first waits for the
+ * problems' own streams, then orders all work on the stream of problems[0]
+ * and returns when it is done.  count is 1..4096.
+ * Errors: INVALID_ARG, CUDA, NONFINITE (some f not finite; all outputs are
+ * written). */
+int octmc_eval_batch(octmc_problem *const *problems, int count, const int *levels, const double *const *disp_dev,
+                     double *const *grad_dev, double *f_host);
+
 /* L-BFGS solve of one level (Sec. 2.1) from the device field disp_inout
  * (overwritten with the result).  eta is first computed from the initial
  * field (Eq. 10).  Returns OK, NOT_CONVERGED (iteration cap) or an error;

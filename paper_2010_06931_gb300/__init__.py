@@ -308,6 +308,29 @@ def enface(octa, oct, fast_axis, v, q_lo=0.05, q_hi=0.95, thresh=0.1, t_oct=None
     return E, dict(p_lo=info[0], p_hi=info[1], t_oct=info[2], kept=int(info[3]))
 
 
+def eval_batch(problems, levels, disps, grads=None):
+    """Objectives of several problems in one batched evaluation
+    (``octmc_eval_batch``): ``problems``, ``levels``, ``disps`` (and
+    optionally ``grads``, tensors receiving the gradients, or None entries)
+    are sequences of equal length; returns the list of f values."""
+    k = len(problems)
+    if not (len(levels) == len(disps) == k) or (grads is not None and len(grads) != k):
+        raise ValueError("problems, levels, disps and grads must have the same length")
+    for P, l, D in zip(problems, levels, disps):
+        _check_disp(D, P.disp_shape(l))
+    if grads is not None:
+        for P, l, g in zip(problems, levels, grads):
+            if g is not None:
+                _check_disp(g, P.disp_shape(l))
+    hs = (C.c_void_p * k)(*[P._h.value for P in problems])
+    lv = (C.c_int * k)(*[int(l) for l in levels])
+    dp = (C.c_void_p * k)(*[D.data_ptr() for D in disps])
+    gp = None if grads is None else (C.c_void_p * k)(*[None if g is None else g.data_ptr() for g in grads])
+    f = (C.c_double * k)()
+    N.check(N.lib().octmc_eval_batch(hs, k, lv, dp, gp, f), "octmc_eval_batch")
+    return list(f)
+
+
 def create_problem(*args, **kw):
     """``octmc_create_problem``: see :class:`Problem`."""
     return Problem(*args, **kw)
@@ -349,9 +372,10 @@ class Server:
     """Continuous-batching solver (``octmc_server_*``).
 
     ``submit`` queues a full coarse-to-fine solve of one scan pair and returns
-    a ticket; ``step`` admits what fits the device-memory budget and runs one
-    batched evaluation step for every admitted request; ``poll`` returns the
-    result of a finished request (and releases it).
+    a ticket; ``step`` retires finished requests and admits what fits the
+    device-memory budget (each admitted request's whole solve runs on the
+    device, concurrently with the others; the call does not wait for it);
+    ``poll`` returns the result of a finished request (and releases it).
     """
 
     QUEUED, RUNNING, DONE, UNKNOWN = 0, 1, 2, -1

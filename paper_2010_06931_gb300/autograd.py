@@ -10,12 +10,15 @@ directions run the library's kernels (``octmc_eval_objective_grad``):
   the backward pass (the interpolation weights are recomputed, nothing of
   size w h d or w h is stored between the passes).
 
+``batch_objective`` sums several independent pairs with one batched
+evaluation (``octmc_eval_batch``) per pass.
+
 The objective is not differentiable twice through this function (the
 backward pass is not itself tracked).
 """
 import torch
 
-__all__ = ["ObjectiveFunction", "objective", "batch_objective"]
+__all__ = ["ObjectiveFunction", "BatchObjectiveFunction", "objective", "batch_objective"]
 
 
 class ObjectiveFunction(torch.autograd.Function):
@@ -50,11 +53,42 @@ def objective(problem, level, disp, mode="save"):
     return ObjectiveFunction.apply(disp, problem, level, mode)
 
 
+class BatchObjectiveFunction(torch.autograd.Function):
+    """Sum of the objectives of several independent pairs, each pass one
+    batched evaluation of all of them (``octmc_eval_batch``: one launch per
+    kernel for the whole batch)."""
+
+    @staticmethod
+    def forward(ctx, problems, level, mode, *disps):
+        from . import eval_batch
+        disps = [D.detach() for D in disps]
+        levels = [level] * len(disps)
+        if mode == "save":
+            grads = [torch.empty_like(D) for D in disps]
+            fs = eval_batch(problems, levels, disps, grads)
+            ctx.save_for_backward(*grads)
+        elif mode == "recompute":
+            fs = eval_batch(problems, levels, disps, None)
+            ctx.save_for_backward(*disps)
+        else:
+            raise ValueError("mode must be 'save' or 'recompute'")
+        ctx.problems, ctx.level, ctx.mode = problems, level, mode
+        return torch.tensor(sum(fs), dtype=torch.float64, device=disps[0].device)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        from . import eval_batch
+        saved = ctx.saved_tensors
+        if ctx.mode == "save":
+            grads = list(saved)
+        else:
+            grads = [torch.empty_like(D) for D in saved]
+            eval_batch(ctx.problems, [ctx.level] * len(saved), list(saved), grads)
+        return (None, None, None) + tuple(grad_out.to(g.dtype) * g for g in grads)
+
+
 def batch_objective(problems, level, disps, mode="recompute"):
     """Sum of the objectives of several independent pairs (one displacement
-    tensor per problem); its backward fills each tensor's ``grad``."""
-    total = None
-    for P, D in zip(problems, disps):
-        f = objective(P, level, D, mode)
-        total = f if total is None else total + f
-    return total
+    tensor per problem) from one batched evaluation per pass; its backward
+    fills each tensor's ``grad``."""
+    return BatchObjectiveFunction.apply(list(problems), level, mode, *disps)

@@ -16,6 +16,8 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "liboctmc.so")
 
 NVCC = os.environ.get("NVCC", "nvcc")
+# extra nvcc flags (e.g. -D switches of the kernels' tuning constants)
+EXTRA = os.environ.get("OCTMC_NVCC_EXTRA", "").split()
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
          "--expt-relaxed-constexpr", "-I", INCLUDE]
@@ -44,7 +46,7 @@ def build(force=False, verbose=False):
     procs = []
     for src in sources():
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [NVCC] + ARCH + FLAGS + ["-c", src, "-o", obj]
+        cmd = [NVCC] + ARCH + FLAGS + EXTRA + ["-c", src, "-o", obj]
         procs.append((src, obj, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     objs, logs = [], []
     for src, obj, p in procs:

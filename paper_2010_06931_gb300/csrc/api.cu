@@ -1346,6 +1346,34 @@ int octmc_eval_objective_grad(octmc_problem* p, int level, const double* disp, d
   return rc;
 }
 
+int octmc_eval_batch(octmc_problem* const* problems, int count, const int* levels, const double* const* disp,
+                     double* const* grad, double* f_host) {
+  if (!problems || !levels || !disp || count < 1 || count > 4096) return OCTMC_ERR_INVALID_ARG;
+  std::vector<EvalReq> reqs;
+  reqs.reserve(count);
+  for (int k = 0; k < count; k++) {
+    octmc_problem* P = problems[k];
+    if (!valid_level(P, levels[k]) || !disp[k]) return OCTMC_ERR_INVALID_ARG;
+    for (int j = 0; j < k; j++)
+      if (problems[j] == P) return OCTMC_ERR_INVALID_ARG;
+    reqs.push_back({P, levels[k], disp[k], grad ? grad[k] : nullptr, nullptr, P->lv[levels[k]].eta,
+                    P->desc.delta0});
+  }
+  return guarded([&] {
+    for (int k = 0; k < count; k++) CK(cudaStreamSynchronize(problems[k]->st));
+    cudaStream_t st = problems[0]->st;
+    eval_batch(st, reqs);
+    CK(cudaStreamSynchronize(st));
+    bool finite = true;
+    for (int k = 0; k < count; k++) {
+      const double f = problems[k]->res_host->terms[4];
+      if (f_host) f_host[k] = f;
+      finite = finite && std::isfinite(f);
+    }
+    return finite ? OCTMC_OK : OCTMC_ERR_NONFINITE;
+  });
+}
+
 int octmc_solve_level(octmc_problem* p, int level, double* disp, octmc_stats* st) {
   if (!valid_level(p, level) || !disp) return OCTMC_ERR_INVALID_ARG;
   return guarded([&] { return solve_impl(p, level, disp, st); });

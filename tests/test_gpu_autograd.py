@@ -83,3 +83,19 @@ def test_batch_of_pairs_with_recomputation():
         assert np.linalg.norm(gb - gc) <= 1e-4 * np.linalg.norm(gc)
     fsum = sum(P.eval_objective_grad(0, D.detach()) for P, D in zip(probs, Ds))
     assert total.item() == pytest.approx(fsum, rel=1e-12)
+    # the batched evaluation (one launch per kernel for all 16 pairs) gives each
+    # member exactly its single evaluation, in both modes
+    singles, sgrads = [], []
+    for P, D in zip(probs, Ds):
+        g = torch.empty_like(D)
+        singles.append(P.eval_objective_grad(0, D.detach(), g))
+        sgrads.append(g)
+    bgrads = [torch.empty_like(D) for D in Ds]
+    fb = octmc.eval_batch(probs, [0] * len(probs), [D.detach() for D in Ds], bgrads)
+    assert fb == singles
+    assert all(torch.equal(a, b) for a, b in zip(bgrads, sgrads))
+    Es = [D.detach().clone().requires_grad_(True) for D in Ds]
+    total_s = batch_objective(probs, 0, Es, mode="save")
+    total_s.backward()
+    assert total_s.item() == total.item()
+    assert all(torch.equal(E.grad, D.grad) for E, D in zip(Es, Ds))
