@@ -858,7 +858,7 @@ cudaGraphNode_t append_level(octmc_problem* P, cudaGraph_t g, cudaGraphNode_t de
   CK(cudaGraphAddNode(&inode, body, &sink, nullptr, 1, &ip));
   capture_after(P, ip.conditional.phGraph_out[0], nullptr, [&](cudaStream_t cs) {
     CK(launch_solve_pair(S, H, P->xt, P->gt, P->x, P->g, n, cs));
-    CK(launch_solve_dots(S, H, P->g, n, P->spartials, P->scounter, cs));
+    CK(launch_solve_dots(S, H, m, P->g, n, P->spartials, P->scounter, cs));
     CK(launch_solve_comb(S, H, P->g, P->dir, n, cs));
   });
   capture_after(P, body, inode, [&](cudaStream_t cs) { CK(launch_solve_loop(S, hw, cs)); });

@@ -385,7 +385,7 @@ cudaError_t launch_solve_post_trial(const SolveState* S, double* xt, double* gt,
 cudaError_t launch_solve_pair(const SolveState* S, const HistSet& H, const double* xt, const double* gt, double* x,
                               double* g, int64_t n, cudaStream_t s);
 int solve_dots_blocks(int64_t n);
-cudaError_t launch_solve_dots(SolveState* S, const HistSet& H, const double* g, int64_t n, double* partials,
+cudaError_t launch_solve_dots(SolveState* S, const HistSet& H, int m, const double* g, int64_t n, double* partials,
                               unsigned* counter, cudaStream_t s);
 cudaError_t launch_solve_comb(const SolveState* S, const HistSet& H, const double* g, double* dir, int64_t n,
                               cudaStream_t s);

@@ -18,11 +18,11 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kChunk = 16;             // history vectors per block row
-constexpr int kPerThread = 8;          // elements per thread (at least)
+constexpr int kChunk = 20;             // history vectors per block row
+constexpr int kPerThread = 4;          // elements per thread on long vectors
+constexpr int kMinBlocks = 152;        // blocks per row: at least one per SM
 constexpr int kMaxBlocks = 8 * 152;    // blocks per row
 constexpr int kMaxVec = 2 * kMaxM + 2; // history vectors of one product pass
-constexpr int kMaxRows = (kMaxVec + kChunk - 1) / kChunk;
 
 __device__ __forceinline__ unsigned long long abs_bits(double v) {
   return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
@@ -127,43 +127,86 @@ __device__ void history_update(SolveState* S) {
   S->gmax = r[2 * K + 2];
 }
 
-// dir = -H g in the compact representation with H0 = gamma I, gamma from the
-// newest pair; returns g . dir (from the products; no extra pass)
-__device__ double direction(SolveState* S) {
+// After the products: history update, stopping tests, and the compact-form
+// (Byrd, Nocedal & Schnabel) direction dir = -H g with H0 = gamma I, gamma
+// from the newest pair, as coefficients of g and the history vectors; g . dir
+// follows from the products (no extra pass).  Run by every thread of one
+// block: the k x k blocks of S'Y and Y'Y are staged in shared memory, the
+// matrix-vector rows are spread over threads, the two triangular solves run
+// in one thread; every sum keeps the serial order, so the result does not
+// depend on the thread count.
+struct Algebra {
+  double R[kMaxM][kMaxM];   // R_ij = s_i . y_j
+  double YY[kMaxM][kMaxM];  // y_i . y_j
+  double a[kMaxM], b[kMaxM], u[kMaxM], w[kMaxM], top[kMaxM];
+  int proceed;
+};
+
+__device__ void after_products(SolveState* S, Algebra& A) {
+  if (threadIdx.x == 0) {
+    const bool accepted = S->mode == kModeAccept;
+    history_update(S);
+    A.proceed = 1;
+    if (accepted && S->small >= 3) {
+      S->status = 0;
+      S->done = 1;
+      A.proceed = 0;
+    } else if (S->iters >= S->max_iter) {
+      S->status = 1;
+      S->done = 1;
+      A.proceed = 0;
+    } else if (S->gmax <= S->gtol) {
+      S->status = 0;
+      S->done = 1;
+      A.proceed = 0;
+    }
+  }
+  __syncthreads();
+  if (!A.proceed) return;
   const int k = S->k;
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    const int i = t / k, j = t % k;
+    A.R[i][j] = SYa(S, S->order[i], S->order[j]);
+    A.YY[i][j] = YYa(S, S->order[i], S->order[j]);
+  }
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    A.a[i] = S->sg[S->order[i]];
+    A.b[i] = S->yg[S->order[i]];
+  }
+  __syncthreads();
+  double gamma = 0.0;
+  if (k > 0) gamma = A.R[k - 1][k - 1] / A.YY[k - 1][k - 1];
+  if (k > 0 && threadIdx.x == 0) {  // u = R^{-1} a (R upper triangular)
+    for (int i = k - 1; i >= 0; i--) {
+      double s = A.a[i];
+      for (int j = i + 1; j < k; j++) s -= A.R[i][j] * A.u[j];
+      A.u[i] = s / A.R[i][i];
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {  // w = (D + gamma Y'Y) u - gamma b
+    double s = A.R[i][i] * A.u[i];
+    for (int j = 0; j < k; j++) s += gamma * A.YY[i][j] * A.u[j];
+    A.w[i] = s - gamma * A.b[i];
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   double gd;
   if (k > 0) {
-    const int last = S->order[k - 1];
-    const double gamma = SYa(S, last, last) / YYa(S, last, last);
-    double a[kMaxM], b[kMaxM], u[kMaxM], wv[kMaxM], top[kMaxM];
-    for (int i = 0; i < k; i++) {
-      a[i] = S->sg[S->order[i]];
-      b[i] = S->yg[S->order[i]];
-    }
-    for (int i = k - 1; i >= 0; i--) {  // u = R^{-1} a, R_ij = s_i . y_j (i <= j)
-      double s = a[i];
-      for (int j = i + 1; j < k; j++) s -= SYa(S, S->order[i], S->order[j]) * u[j];
-      u[i] = s / SYa(S, S->order[i], S->order[i]);
-    }
-    for (int i = 0; i < k; i++) {  // w = (D + gamma Y'Y) u - gamma b
-      double s = SYa(S, S->order[i], S->order[i]) * u[i];
-      for (int j = 0; j < k; j++) s += gamma * YYa(S, S->order[i], S->order[j]) * u[j];
-      wv[i] = s - gamma * b[i];
-    }
     for (int i = 0; i < k; i++) {  // top = R^{-T} w
-      double s = wv[i];
-      for (int j = 0; j < i; j++) s -= SYa(S, S->order[j], S->order[i]) * top[j];
-      top[i] = s / SYa(S, S->order[i], S->order[i]);
+      double s = A.w[i];
+      for (int j = 0; j < i; j++) s -= A.R[j][i] * A.top[j];
+      A.top[i] = s / A.R[i][i];
     }
     S->cg = -gamma;
     S->nc = 0;
     gd = -gamma * S->gg;
     for (int i = 0; i < k; i++) {
       S->hid[S->nc] = 2 * S->order[i];
-      S->coef[S->nc++] = -top[i];
+      S->coef[S->nc++] = -A.top[i];
       S->hid[S->nc] = 2 * S->order[i] + 1;
-      S->coef[S->nc++] = gamma * u[i];
-      gd += -top[i] * a[i] + gamma * u[i] * b[i];
+      S->coef[S->nc++] = gamma * A.u[i];
+      gd += -A.top[i] * A.a[i] + gamma * A.u[i] * A.b[i];
     }
     if (!(gd < 0.0)) {  // not a descent direction: drop the history, -g
       S->k = 0;
@@ -176,28 +219,7 @@ __device__ double direction(SolveState* S) {
     S->nc = 0;
     gd = -S->gg;
   }
-  return gd;
-}
-
-__device__ void after_products(SolveState* S) {
-  const bool accepted = S->mode == kModeAccept;
-  history_update(S);
-  if (accepted && S->small >= 3) {
-    S->status = 0;
-    S->done = 1;
-    return;
-  }
-  if (S->iters >= S->max_iter) {
-    S->status = 1;
-    S->done = 1;
-    return;
-  }
-  if (S->gmax <= S->gtol) {
-    S->status = 0;
-    S->done = 1;
-    return;
-  }
-  S->dg0 = direction(S);
+  S->dg0 = gd;
   S->a = (S->k == 0) ? 1.0 / sqrt(S->gg) : 1.0;
   S->lo = 0.0;
   S->hi = INFINITY;
@@ -208,10 +230,12 @@ __device__ void after_products(SolveState* S) {
 
 // Products of the candidate history vectors (the stored pairs and, after an
 // accepted step, the new one) with the probes y_new (accepted step only) and
-// g; g . g and max|g|.  Grid (G, rows): block (bx, r) takes candidates
-// r*16 .. r*16+15 over a strided share of the elements; the last block to
-// finish adds the block partials (fixed trees) and runs the algebra.
-__global__ void __launch_bounds__(kThreads) dots_kernel(SolveState* S, const HistSet H, const double* __restrict__ g,
+// g; g . g and max|g|.  Grid (G, rows), rows enough for the problem's
+// longest history: block (bx, r) takes candidates r*20 .. r*20+19 over a
+// strided share of the elements (rows beyond this step's candidates only
+// arrive); the last block to finish adds the block partials (fixed trees)
+// and runs the algebra.
+__global__ void __launch_bounds__(kThreads, 2) dots_kernel(SolveState* S, const HistSet H, const double* __restrict__ g,
                                                         int64_t n, double* partials, unsigned* counter) {
   __shared__ double sm[(2 * kChunk + 3) * kWarps];
   __shared__ bool is_last;
@@ -223,6 +247,12 @@ __global__ void __launch_bounds__(kThreads) dots_kernel(SolveState* S, const His
   const int k0 = blockIdx.y * kChunk;
   const int kn = min(kChunk, K - k0);
   const bool first = blockIdx.y == 0;
+  if (kn <= 0 && !first) {  // a row beyond this step's vectors: only arrive
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = (atomicAdd(counter, 1u) == gridDim.x * gridDim.y - 1);
+    __syncthreads();
+    if (!is_last) return;
+  } else {
   const double* q0 = accepted ? H.Y[S->spare] : nullptr;
   const double* h[kChunk];
 #pragma unroll
@@ -304,7 +334,9 @@ __global__ void __launch_bounds__(kThreads) dots_kernel(SolveState* S, const His
   if (threadIdx.x == 0) is_last = (atomicAdd(counter, 1u) == gridDim.x * gridDim.y - 1);
   __syncthreads();
   if (!is_last) return;
+  }
   __threadfence();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nout = 2 * K + 3;
   for (int o = warp; o < nout; o += kWarps) {
     const bool is_max = (o == nout - 1);
@@ -325,20 +357,29 @@ __global__ void __launch_bounds__(kThreads) dots_kernel(SolveState* S, const His
     *counter = 0u;
     S->ncand = ncand;
     for (int t = 0; t < ncand; t++) S->cand[t] = (t < nstored) ? S->order[t] : S->spare;
-    after_products(S);
   }
+  __syncthreads();
+  __shared__ Algebra alg;
+  after_products(S, alg);
 }
 
 // dir = cg g + sum_j coef_j h_j (float64, terms in a fixed order)
 __global__ void __launch_bounds__(kThreads) comb_kernel(const SolveState* __restrict__ S, const HistSet H,
                                                         const double* __restrict__ g, double* __restrict__ dir,
                                                         int64_t n) {
+  __shared__ const double* hp[kMaxVec];
+  __shared__ double cf[kMaxVec];
   if (S->done) return;
   const int nc = S->nc;
   const double cg = S->cg;
+  if (threadIdx.x < nc) {
+    hp[threadIdx.x] = hvec(H, S->hid[threadIdx.x]);
+    cf[threadIdx.x] = S->coef[threadIdx.x];
+  }
+  __syncthreads();
   for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < n; e += (int64_t)gridDim.x * kThreads) {
     double s = 0.0;
-    for (int j = 0; j < nc; j++) s = fma(S->coef[j], hvec(H, S->hid[j])[e], s);
+    for (int j = 0; j < nc; j++) s = fma(cf[j], hp[j][e], s);
     dir[e] = fma(cg, g[e], s);
   }
 }
@@ -405,9 +446,12 @@ inline unsigned grid_for(int64_t n) {
 
 }  // namespace
 
+// The products are float64 work, which this GPU runs at 1/64 of the float
+// rate per SM: every SM takes a share (at least one block each), with about
+// kPerThread elements per thread on long vectors.
 int solve_dots_blocks(int64_t n) {
   int64_t b = (n + (int64_t)kThreads * kPerThread - 1) / ((int64_t)kThreads * kPerThread);
-  if (b < 1) b = 1;
+  if (b < kMinBlocks) b = kMinBlocks;
   if (b > kMaxBlocks) b = kMaxBlocks;
   return (int)b;
 }
@@ -430,9 +474,11 @@ cudaError_t launch_solve_pair(const SolveState* S, const HistSet& H, const doubl
   return cudaGetLastError();
 }
 
-cudaError_t launch_solve_dots(SolveState* S, const HistSet& H, const double* g, int64_t n, double* partials,
+cudaError_t launch_solve_dots(SolveState* S, const HistSet& H, int m, const double* g, int64_t n, double* partials,
                               unsigned* counter, cudaStream_t s) {
-  dots_kernel<<<dim3(solve_dots_blocks(n), kMaxRows), kThreads, 0, s>>>(S, H, g, n, partials, counter);
+  if (m < 1 || m > kMaxM) return cudaErrorInvalidValue;
+  const int rows = (2 * (m + 1) + kChunk - 1) / kChunk;
+  dots_kernel<<<dim3(solve_dots_blocks(n), rows), kThreads, 0, s>>>(S, H, g, n, partials, counter);
   return cudaGetLastError();
 }
 
