@@ -361,7 +361,8 @@ int octmc_profile_read(octmc_problem *p, double *total_ms, long long *launches);
  * S^str = sum (1 - delta) sum_k L(R_ijk) and S^ang = sum delta d L(R_ij(A))
  * (Eq. 5, 6) of one grid and eta*S^str + S^ang/eta's gradient with respect
  * to the displacements, using the same kernel as the other entry points.
- *   sx, sy: device float32 [h][w][d] with d a multiple of 4 (>= 4);
+ *   sx, sy: device float32 [h][w][d] with d a multiple of 4 (>= 4), 16-byte
+ *           aligned;
  *   ax, ay: device [h][w] or both NULL; vx[h], vy[w]: device or NULL;
  *   disp: device float64 [2][3][h][w];
  *   grad_out: device float64 [2][3][h][w] or NULL (data-term gradient);

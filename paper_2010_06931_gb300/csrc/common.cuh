@@ -213,7 +213,7 @@ constexpr int kModeInit = 0;    // evaluate the start point of the level
 constexpr int kModeTrial = 1;   // evaluate x + a dir
 constexpr int kModeAccept = 2;  // branch: take the accepted trial, new pair, new direction
 constexpr int kModeRetry = 3;   // branch: history dropped, direction -g
-struct SolveState {
+struct __align__(8) SolveState {
   // configuration (set by the host before each launch)
   int64_t n;
   int m, max_iter, max_ls, max_evals;

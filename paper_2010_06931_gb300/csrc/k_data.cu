@@ -10,7 +10,11 @@
 // over depth in the same pass.  The en-face angiography term (Eq. 6), the
 // resampled validity (Eq. 7) and delta (Eq. 8) are per-A-scan scalars.
 //
-// Mapping: one warp per output A-scan.  Depth is processed in blocks of 116
+// Mapping: one warp per output A-scan; a block's 8 warps take a tile of
+// 4 x 2 neighbouring A-scans (their 4 x 4 neighbourhoods overlap, which the
+// L1 cache turns into hits); 64 registers per thread, so 4 blocks (32 warps)
+// per SM keep loads in flight -- the kernel waits on memory latency more
+// than on arithmetic.  Depth is processed in blocks of 116
 // outputs; lane L (1..29) owns outputs kb + 4(L-1) .. +3.  Each lane loads
 // one aligned group of 4 input samples from each of the 16 transverse
 // neighbour columns with one 128-bit load per column (coalesced along depth
@@ -29,18 +33,15 @@ namespace octmc {
 namespace {
 
 #ifndef OCTMC_DATA_MINB
-#define OCTMC_DATA_MINB 3
+#define OCTMC_DATA_MINB 4
 #endif
-// The whole data-term computation of output A-scan p by one warp.
+// The data-term computation of output A-scan p by one warp (base and frac:
+// the coordinate split of its 6 displacement values).
 template <typename T>
-__device__ __forceinline__ void data_ascan(const DataArgs& A, int64_t p, int lane) {
+__device__ __forceinline__ void data_core(const DataArgs& A, int64_t p, int lane, const int base[6],
+                                          const float frac[6]) {
   const LevelDev& L = A.L;
   const int64_t nasc = (int64_t)L.w * L.h;
-  const int i = (int)(p % L.w), j = (int)(p / L.w);
-
-  int base[6];
-  float frac[6];
-  split_displacement(A.disp, nasc, p, i, j, L, lane, base, frac);
   Vol VX, VY;
   setup_vol(VX, L.sx, L, base, frac);
   setup_vol(VY, L.sy, L, base + 3, frac + 3);
@@ -48,7 +49,9 @@ __device__ __forceinline__ void data_ascan(const DataArgs& A, int64_t p, int lan
   const float inv_eps = 1.0f / A.eps_h;
   const bool ssd = (A.loss == OCTMC_LOSS_SSD);
   float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int kb = 0; kb < L.d; kb += kOutPerIter) {
+  const int nst = (L.d + kOutPerIter - 1) / kOutPerIter;
+  for (int s = 0; s < nst; s++) {
+    const int kb = s * kOutPerIter;
     float IX[4], IzX[4], IxX[4], IyX[4], IY[4], IzY[4], IxY[4], IyY[4];
     sample_block<T>(VX, kb, lane, L.dp, IX, IzX, IxX, IyX);
     sample_block<T>(VY, kb, lane, L.dp, IY, IzY, IxY, IyY);
@@ -160,25 +163,54 @@ __device__ __forceinline__ void data_ascan(const DataArgs& A, int64_t p, int lan
   else if (lane < 8 && A.grad) A.grad[(int64_t)(lane - 2) * nasc + p] = out;
 }
 
+// Output A-scan p by one warp from the volumes in global memory.
+template <typename T>
+__device__ __forceinline__ void data_ascan(const DataArgs& A, int64_t p, int lane) {
+  const LevelDev& L = A.L;
+  const int64_t nasc = (int64_t)L.w * L.h;
+  int base[6];
+  float frac[6];
+  split_displacement(A.disp, nasc, p, (int)(p % L.w), (int)(p / L.w), L, lane, base, frac);
+  data_core<T>(A, p, lane, base, frac);
+}
+
+#ifndef OCTMC_DTILE_X
+#define OCTMC_DTILE_X 4
+#endif
+constexpr int kDTileX = OCTMC_DTILE_X;  // direct kernel: a block's 8 A-scans as kDTileX x (8 / kDTileX)
+constexpr int kDTileY = kWarpsPerBlock / kDTileX;
+
+// A-scan of warp `warp` of direct block b: tiles of kDTileX x kDTileY.
+__device__ __forceinline__ int64_t direct_ascan(const LevelDev& L, int b, int warp) {
+  const int tiles_x = (L.w + kDTileX - 1) / kDTileX;
+  const int i = (b % tiles_x) * kDTileX + warp % kDTileX, j = (b / tiles_x) * kDTileY + warp / kDTileX;
+  return (i < L.w && j < L.h) ? (int64_t)j * L.w + i : -1;
+}
+
+__host__ __device__ inline int64_t direct_blocks(int w, int h) {
+  return (int64_t)((w + kDTileX - 1) / kDTileX) * ((h + kDTileY - 1) / kDTileY);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kWarpsPerBlock * kWarp, OCTMC_DATA_MINB)
 data_kernel(const DataArgs A) {
-  const int64_t p = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-  if (p >= (int64_t)A.L.w * A.L.h) return;  // warp-uniform
+  const int64_t p = direct_ascan(A.L, blockIdx.x, threadIdx.x >> 5);
+  if (p < 0) return;  // warp-uniform
   data_ascan<T>(A, p, threadIdx.x & 31);
 }
 
 // Several problems ("slots") in one launch: grid (x, slots), block
-// (x, s) takes A-scans x*8 .. x*8+7 of slot s (blocks past a slot's end exit
-// at once).  The slots' arguments travel in the kernel's parameter block and
+// (x, s) takes tile x of slot s (blocks past a slot's last tile exit at
+// once).  The slots' arguments travel in the kernel's parameter block and
 // the slot index is uniform per block.  Each A-scan's result does not depend
 // on which other slots are in the launch.
 template <typename T>
 __global__ void __launch_bounds__(kWarpsPerBlock * kWarp, OCTMC_DATA_MINB)
 data_multi_kernel(const __grid_constant__ DataMulti M) {
   const DataArgs& A = M.da[blockIdx.y];
-  const int64_t p = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-  if (p >= (int64_t)A.L.w * A.L.h) return;  // warp-uniform
+  if ((int64_t)blockIdx.x >= direct_blocks(A.L.w, A.L.h)) return;
+  const int64_t p = direct_ascan(A.L, blockIdx.x, threadIdx.x >> 5);
+  if (p < 0) return;  // warp-uniform
   data_ascan<T>(A, p, threadIdx.x & 31);
 }
 
@@ -186,9 +218,8 @@ data_multi_kernel(const __grid_constant__ DataMulti M) {
 
 cudaError_t launch_data_multi(const DataMulti& M, int dtype, cudaStream_t s) {
   if (M.nslots <= 0) return cudaSuccess;
-  int64_t most = 0;
-  for (int k = 0; k < M.nslots; k++) most = max(most, (int64_t)M.da[k].L.w * M.da[k].L.h);
-  const int64_t bx = (most + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  int64_t bx = 0;
+  for (int k = 0; k < M.nslots; k++) bx = max(bx, direct_blocks(M.da[k].L.w, M.da[k].L.h));
   if (bx <= 0) return cudaSuccess;
   const dim3 g((unsigned)bx, (unsigned)M.nslots);
   if (dtype == OCTMC_BF16)
@@ -201,8 +232,7 @@ cudaError_t launch_data_multi(const DataMulti& M, int dtype, cudaStream_t s) {
 }
 
 cudaError_t launch_data(const DataArgs& a, cudaStream_t s) {
-  const int64_t nasc = (int64_t)a.L.w * a.L.h;
-  const int64_t blocks = (nasc + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  const int64_t blocks = direct_blocks(a.L.w, a.L.h);
   if (blocks <= 0) return cudaSuccess;
   if (a.L.dtype == OCTMC_BF16)
     data_kernel<__nv_bfloat16><<<(unsigned)blocks, kWarpsPerBlock * kWarp, 0, s>>>(a);

@@ -19,7 +19,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kChunk = 20;             // history vectors per block row
-constexpr int kPerThread = 4;          // elements per thread on long vectors
+constexpr int kPerThread = 8;          // elements per thread on long vectors
 constexpr int kMinBlocks = 152;        // blocks per row: at least one per SM
 constexpr int kMaxBlocks = 8 * 152;    // blocks per row
 constexpr int kMaxVec = 2 * kMaxM + 2; // history vectors of one product pass
@@ -336,6 +336,15 @@ __global__ void __launch_bounds__(kThreads, 2) dots_kernel(SolveState* S, const 
   if (!is_last) return;
   }
   __threadfence();
+  // the epilogue works on a shared-memory copy of the state: its serial parts
+  // would otherwise wait on L2 for every dependent access
+  __shared__ SolveState sS;
+  {
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(S);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(&sS);
+    for (int t = threadIdx.x; t < (int)(sizeof(SolveState) / 8); t += kThreads) dst[t] = src[t];
+  }
+  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nout = 2 * K + 3;
   for (int o = warp; o < nout; o += kWarps) {
@@ -350,17 +359,23 @@ __global__ void __launch_bounds__(kThreads, 2) dots_kernel(SolveState* S, const 
     v = warp_sum(v);
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, s));
-    if (lane == 0) S->dots[o] = is_max ? __longlong_as_double((long long)m) : v;
+    if (lane == 0) sS.dots[o] = is_max ? __longlong_as_double((long long)m) : v;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     *counter = 0u;
-    S->ncand = ncand;
-    for (int t = 0; t < ncand; t++) S->cand[t] = (t < nstored) ? S->order[t] : S->spare;
+    sS.ncand = ncand;
+    for (int t = 0; t < ncand; t++) sS.cand[t] = (t < nstored) ? sS.order[t] : sS.spare;
   }
   __syncthreads();
   __shared__ Algebra alg;
-  after_products(S, alg);
+  after_products(&sS, alg);
+  __syncthreads();
+  {
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&sS);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(S);
+    for (int t = threadIdx.x; t < (int)(sizeof(SolveState) / 8); t += kThreads) dst[t] = src[t];
+  }
 }
 
 // dir = cg g + sum_j coef_j h_j (float64, terms in a fixed order)

@@ -12,6 +12,7 @@
 // address is looked up with cudaGetSymbolAddress, for the current device,
 // on every call, and passed to the kernels.
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 
 #include "common.cuh"
@@ -107,6 +108,8 @@ extern "C" int octmc_data_term_static(const float* sx, const float* sy, const fl
   if (!sx || !sy || !disp || !sums_out || w < 1 || h < 1 || d < 4 || (d & 3) != 0)
     return OCTMC_ERR_INVALID_ARG;
   if ((ax == nullptr) != (ay == nullptr)) return OCTMC_ERR_INVALID_ARG;
+  // the kernel reads the volumes in aligned 16-byte groups of 4 samples
+  if ((reinterpret_cast<uintptr_t>(sx) & 15u) || (reinterpret_cast<uintptr_t>(sy) & 15u)) return OCTMC_ERR_INVALID_ARG;
   if (!(eta > 0) || !(eps_h > 0) || !(delta0 >= 0) || !std::isfinite(eta) || !std::isfinite(eps_h) ||
       !std::isfinite(delta0))
     return OCTMC_ERR_INVALID_ARG;

@@ -216,12 +216,12 @@ __device__ __forceinline__ void axial(const float4& T, const float4& Tx, const f
 }
 
 // Interpolated values (and their displacement derivatives) of one volume
-// at the lane's 4 outputs of the depth block starting at kb.
+// at the lane's 4 outputs.  qk: first input depth of the lane's group
+// (samples, may lie outside the volume); qc: index of that group's (clamped)
+// samples in the volume.
 template <typename S>
-__device__ __forceinline__ void sample_block(const Vol& V, int kb, int lane, int dp, float I[4],
-                                             float Iz[4], float Ix[4], float Iy[4]) {
-  const int qk = kb + 4 * V.q + 4 * (lane - 1);  // first input depth of the lane's group
-  const unsigned qc = (unsigned)(min(max(qk, 0), dp - 4) >> 2);
+__device__ __forceinline__ void sample_group(const Vol& V, int qk, unsigned qc, int dp, float I[4], float Iz[4],
+                                             float Ix[4], float Iy[4]) {
   // transverse 4 x 4 interpolation of the group and its x / y derivatives,
   // in packed pairs along depth (same operations and order as scalar FMAs)
   Q4 Tq = q4zero(), Txq = q4zero(), Tyq = q4zero();
@@ -230,7 +230,8 @@ __device__ __forceinline__ void sample_block(const Vol& V, int kb, int lane, int
     Q4 U = q4zero(), Ux = q4zero();
 #pragma unroll
     for (int a = 0; a < 4; a++) {
-      const Q4 s = q4(load4<S>(V.base, V.roff[b] + V.coff[a] + qc));
+      const unsigned idx = V.roff[b] + V.coff[a] + qc;
+      const Q4 s = q4(load4<S>(V.base, idx));
       qfma(U, make_float2(V.wx[a], V.wx[a]), s);
       qfma(Ux, make_float2(V.dwx[a], V.dwx[a]), s);
     }
@@ -251,6 +252,17 @@ __device__ __forceinline__ void sample_block(const Vol& V, int kb, int lane, int
     case 2: axial<2>(T, Tx, Ty, V.wz, V.dwz, I, Iz, Ix, Iy); break;
     default: axial<3>(T, Tx, Ty, V.wz, V.dwz, I, Iz, Ix, Iy); break;
   }
+}
+
+// Interpolated values (and their displacement derivatives) of one volume
+// at the lane's 4 outputs of the depth block starting at kb, from the
+// volume in global memory.
+template <typename S>
+__device__ __forceinline__ void sample_block(const Vol& V, int kb, int lane, int dp, float I[4],
+                                             float Iz[4], float Ix[4], float Iy[4]) {
+  const int qk = kb + 4 * V.q + 4 * (lane - 1);  // first input depth of the lane's group
+  const unsigned qc = (unsigned)(min(max(qk, 0), dp - 4) >> 2);
+  sample_group<S>(V, qk, qc, dp, I, Iz, Ix, Iy);
 }
 
 }  // namespace

@@ -18,66 +18,87 @@
 
 namespace octmc {
 
+// The controller fields are read once (independent loads) and written back
+// once: this runs in a single thread on state in global memory, where every
+// dependent access would cost a round trip to L2.
 __device__ __forceinline__ void ls_decide(SolveState* S, double ft, double dgt, cudaGraphConditionalHandle h_branch) {
-  S->save_best = 0;
-  S->restore_best = 0;
-  S->evals++;
-  int branch = 0;
-  if (S->mode == kModeInit) {
-    S->f = ft;
-    S->ft = ft;
+  const int mode0 = S->mode, max_ls = S->max_ls, max_evals = S->max_evals, k0 = S->k;
+  int ls = S->ls, evals = S->evals + 1, have_lo = S->have_lo, retried = S->retried;
+  int iters = S->iters, small = S->small, status = S->status, done = S->done, mode = mode0, k = k0;
+  double f = S->f, fb = S->fb, a = S->a, lo = S->lo, hi = S->hi;
+  const double dg0 = S->dg0, ftol = S->ftol;
+  int save_best = 0, restore_best = 0, branch = 0;
+  double ftn = ft;
+  if (mode0 == kModeInit) {
+    f = ft;
     branch = 1;
   } else {
-    S->ft = ft;
-    S->ls++;
-    const double a = S->a;
+    ls++;
+    const double at = a;
     bool accepted = false;
-    if (!(ft <= S->f + 1e-4 * a * S->dg0)) {
-      S->hi = a;
-      S->a = 0.5 * (S->lo + S->hi);
-    } else if (dgt < 0.9 * S->dg0) {
-      S->lo = a;
-      S->have_lo = 1;
-      S->fb = ft;
-      S->save_best = 1;
-      S->a = isinf(S->hi) ? 2.0 * a : 0.5 * (S->lo + S->hi);
+    if (!(ft <= f + 1e-4 * at * dg0)) {
+      hi = at;
+      a = 0.5 * (lo + hi);
+    } else if (dgt < 0.9 * dg0) {
+      lo = at;
+      have_lo = 1;
+      fb = ft;
+      save_best = 1;
+      a = isinf(hi) ? 2.0 * at : 0.5 * (lo + hi);
     } else {
       accepted = true;
     }
-    if (!accepted && S->ls < S->max_ls && S->evals < S->max_evals) {
+    if (!accepted && ls < max_ls && evals < max_evals) {
       branch = 0;  // next trial with the new step
     } else {
       if (!accepted) {
-        if (S->have_lo) {
-          S->restore_best = 1;
-          S->ft = S->fb;
+        if (have_lo) {
+          restore_best = 1;
+          ftn = fb;
           accepted = true;
-        } else if (S->k > 0 && !S->retried) {
-          S->k = 0;  // drop the history, retry from -g
-          S->retried = 1;
-          S->mode = kModeRetry;
+        } else if (k > 0 && !retried) {
+          k = 0;  // drop the history, retry from -g
+          retried = 1;
+          mode = kModeRetry;
           branch = 1;
         } else {
-          S->status = 2;
-          S->done = 1;
+          status = 2;
+          done = 1;
         }
       }
       if (accepted) {
-        S->retried = 0;
-        const double fo = S->f, fn = S->ft;
-        const double rel = (fo - fn) / fmax(fmax(fabs(fo), fabs(fn)), 1.0);
-        S->f = fn;
-        S->iters++;
-        S->small = (rel < S->ftol) ? S->small + 1 : 0;
-        S->mode = kModeAccept;
+        retried = 0;
+        const double rel = (f - ftn) / fmax(fmax(fabs(f), fabs(ftn)), 1.0);
+        f = ftn;
+        iters++;
+        small = (rel < ftol) ? small + 1 : 0;
+        mode = kModeAccept;
         branch = 1;
       }
     }
   }
-  if (S->evals >= S->max_evals && !S->done && branch == 0) {
-    S->status = 2;
-    S->done = 1;
+  if (evals >= max_evals && !done && branch == 0) {
+    status = 2;
+    done = 1;
   }
+  S->save_best = save_best;
+  S->restore_best = restore_best;
+  S->evals = evals;
+  S->ls = ls;
+  S->have_lo = have_lo;
+  S->retried = retried;
+  S->iters = iters;
+  S->small = small;
+  S->status = status;
+  S->done = done;
+  S->mode = mode;
+  S->k = k;
+  S->f = f;
+  S->ft = ftn;
+  S->fb = fb;
+  S->a = a;
+  S->lo = lo;
+  S->hi = hi;
   S->branch = branch;
   cudaGraphSetConditional(h_branch, branch ? 1u : 0u);
 }
