@@ -117,9 +117,9 @@ def parse_args():
     ap.add_argument("--serve", action="store_true",
                     help="only the serving leg: Poisson arrivals of mixed-size BF16 pairs")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
-    ap.add_argument("--serve-requests", type=int, default=12)
+    ap.add_argument("--serve-requests", type=int, default=6)
     ap.add_argument("--serve-rate", type=float, default=4.0)
-    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-slots", type=int, default=3)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     return ap.parse_args()
 
@@ -588,7 +588,7 @@ def serve_leg(args, octmc):
     pairs solved one after another in float32."""
     import torch
     from paper_2010_06931_gb300.serving import serve_poisson
-    pool, truth = serve_pool(2)
+    pool, truth = serve_pool(max(1, (args.serve_requests + 2) // 3))
     kw = dict(levels=3)
     reqs = [dict(**pool[k % len(pool)], storage=octmc.BF16, **kw) for k in range(args.serve_requests)]
     server = octmc.Server(budget_bytes=int(args.serve_budget_gb * 1e9), max_slots=args.serve_slots)
