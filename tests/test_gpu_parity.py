@@ -329,3 +329,48 @@ def test_eval_parity_clinical_size(c2):
     T, _ = true_displacement(p, cfg["w"], cfg["h"])
     compare_eval(p, T)
     compare_eval(p, T + np.random.default_rng(4).normal(0.0, 0.5, T.shape), loss=1, alpha=0.1)
+
+
+def test_solve_full_converged_minimum_clinical_size(c2):
+    # the benchmark's converged solve (300 x 300 A-scans x 512, three levels,
+    # library defaults) against the FP64 oracle's converged solve stored in
+    # tests/golden/c2_oracle_solution.npz.  This objective is non-convex and its
+    # minimum is not determined to 0.05 px: two GPU solves whose inputs differ
+    # by 1e-7 relative end 0.24 px RMS apart (0.28 at ftol 1e-8 and 1e-9), and
+    # a GPU solve started at the oracle's minimum moves 0.19 px.  Most A-scans
+    # agree closely; patches of a tenth of them settle in neighbouring minima.
+    # Pinned: both converge, the GPU's minimum is at least as deep as the
+    # oracle's in the FP64 objective (same eta), the median A-scan agrees within
+    # 0.05 px, and the whole field within twice the perturbation spread
+    import hashlib
+    import json
+    import os
+    p, cfg = c2
+    path = os.path.join(os.path.dirname(__file__), "golden", "c2_oracle_solution.npz")
+    z = np.load(path)
+    ref = z["disp"].astype(np.float64)
+    meta = json.loads(str(z["meta"]))
+    h = hashlib.sha1()
+    for k in ("sx", "sy", "ax", "ay", "vx", "vy", "tx", "ty"):
+        h.update(np.ascontiguousarray(p[k]).tobytes())
+    assert h.hexdigest() == meta["inputs_sha1"], "stored solve is of other inputs"
+    assert [s["status"] for s in meta["stats"]] == [0, 0, 0]
+    G = gpu_problem(p, levels=meta["levels"], lbfgs_m=meta["solver"]["m"],
+                    ftol=meta["solver"]["ftol"])
+    Dg, st = G.solve_full()
+    Dg = Dg.cpu().numpy().astype(np.float64)
+    assert [s["status"] for s in st] == [0, 0, 0], st
+    diff = Dg - ref
+    rms = float(np.sqrt((diff ** 2).mean()))
+    per_ascan = np.sqrt((diff.reshape(6, -1) ** 2).mean(axis=0))
+    med = float(np.median(per_ascan))
+    C = cpu_problem(p)
+    C.eta = meta["stats"][-1]["eta"]
+    f_g = C.eval(Dg, grad=False)[0]
+    f_o = meta["stats"][-1]["f"]
+    print("c2 converged: GPU vs oracle %.4f px RMS, median A-scan %.4f px; FP64 objective "
+          "%.3f (GPU) / %.3f (oracle); iters %s / %s" %
+          (rms, med, f_g, f_o, [s["iters"] for s in st], [s["iters"] for s in meta["stats"]]))
+    assert f_g <= f_o * (1.0 + 1e-5)
+    assert med <= 0.05
+    assert rms <= 0.5
