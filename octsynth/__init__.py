@@ -30,5 +30,6 @@ All arrays are in the common frame: volumes ``[h][w][d]`` (depth contiguous),
 images and time maps ``[h][w]``; ``vx`` has one value per row (the X-fast
 scan's B-scans are rows), ``vy`` one per column.
 """
-from .generator import CONFIGS, make_pair, make_config, true_displacement  # noqa: F401
+from .generator import (CONFIGS, fingerprint, fingerprints_match, make_config, make_pair,  # noqa: F401
+                        true_displacement)
 from .octa import make_octa_scan  # noqa: F401

@@ -340,3 +340,39 @@ def true_displacement(pair, w, h, iters=60):
             hi = b + max(m[sl - 1, slow], m[sl, slow]) - c[slow] + 2.5
             mask[V] &= ~((pos >= lo) & (pos <= hi))
     return disp, mask
+
+
+INPUT_KEYS = ("sx", "sy", "ax", "ay", "vx", "vy", "tx", "ty")
+
+
+def fingerprint(pair):
+    """Per input array of a pair: its float64 sum and sum of squares.
+
+    Equal renderings on two platforms may differ in the last bits of some
+    voxels (their numpy builds round transcendental functions differently),
+    so stored results are matched to their inputs by these sums to a relative
+    tolerance rather than by a checksum of the bytes."""
+    out = {}
+    for k in INPUT_KEYS:
+        a = pair.get(k)
+        if a is None:
+            continue
+        a = np.asarray(a, dtype=np.float64)
+        out[k] = [float(a.sum()), float((a * a).sum())]
+    return out
+
+
+def fingerprints_match(a, b, rel=3e-7):
+    """True when two fingerprints name the same arrays with sums equal to
+    ``rel`` relative.  Last-bit differences of a float32 rendering move a sum
+    by at most 2^-23 = 1.2e-7 relative and a sum of squares by twice that
+    (every voxel one ulp off in the same direction); another seed, preset or
+    generator moves them far more.  A sum does not see a small edit of a
+    single voxel."""
+    if not a or not b or set(a) != set(b):
+        return False
+    for k in a:
+        for x, y in zip(a[k], b[k]):
+            if abs(x - y) > rel * max(abs(x), abs(y), 1e-300):
+                return False
+    return True

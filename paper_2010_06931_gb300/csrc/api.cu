@@ -712,11 +712,13 @@ void ensure_solver(octmc_problem* P) {
 // ------------------------------------------------------------ device-resident solve
 // A solve is one CUDA graph.  Per level: the start-field evaluation for eta
 // (Eq. 10), a one-thread kernel that sets eta and the controller state, and
-// a WHILE node whose body evaluates one trial point (trial kernel, mean-term
-// sums forked onto a side stream, data kernel, regulariser kernel with the
-// line-search decision in its last block, keep/restore of the best point)
-// and, under an IF node set by that decision, the accepted-step branch
-// (history pair, products and compact-form direction, direction); a stats
+// a WHILE node whose body evaluates one trial point (trial kernel, which
+// also saves the previous trial when the line search kept it as its best
+// point; mean-term sums forked onto a side stream, data kernel, regulariser
+// kernel with the line-search decision in its last block) and, under an IF
+// node set by that decision, the accepted-step branch (history pair from the
+// trial or the restored best point, products and compact-form direction,
+// direction); a stats
 // kernel closes the level, and the next finer level starts with the
 // prolongation.  The host launches the graph once, synchronises once and
 // reads the per-level statistics.  Graphs are built on first use and kept
@@ -845,9 +847,8 @@ cudaGraphNode_t append_level(octmc_problem* P, cudaGraph_t g, cudaGraphNode_t de
   CK(cudaGraphConditionalHandleCreate(&hb, body, 0, cudaGraphCondAssignDefault));
   const double* eta_dev = &S->eta;
   const cudaGraphNode_t sink = capture_after(P, body, nullptr, [&](cudaStream_t cs) {
-    CK(launch_solve_trial(S, P->x, P->dir, P->xt, n, cs));
+    CK(launch_solve_trial(S, P->x, P->dir, P->xt, P->gt, P->xb, P->gb, n, cs));
     capture_eval(P, cs, l, P->xt, P->gt, P->dir, 1.0, eta_dev, D.delta0, S, hb);
-    CK(launch_solve_post_trial(S, P->xt, P->gt, P->xb, P->gb, n, cs));
   });
   cudaGraphNodeParams ip{};
   ip.type = cudaGraphNodeTypeConditional;
@@ -857,7 +858,7 @@ cudaGraphNode_t append_level(octmc_problem* P, cudaGraph_t g, cudaGraphNode_t de
   cudaGraphNode_t inode;
   CK(cudaGraphAddNode(&inode, body, &sink, nullptr, 1, &ip));
   capture_after(P, ip.conditional.phGraph_out[0], nullptr, [&](cudaStream_t cs) {
-    CK(launch_solve_pair(S, H, P->xt, P->gt, P->x, P->g, n, cs));
+    CK(launch_solve_pair(S, H, P->xt, P->gt, P->xb, P->gb, P->x, P->g, n, cs));
     CK(launch_solve_dots(S, H, m, P->g, n, P->spartials, P->scounter, cs));
     CK(launch_solve_comb(S, H, P->g, P->dir, n, cs));
   });

@@ -213,7 +213,7 @@ constexpr int kModeInit = 0;    // evaluate the start point of the level
 constexpr int kModeTrial = 1;   // evaluate x + a dir
 constexpr int kModeAccept = 2;  // branch: take the accepted trial, new pair, new direction
 constexpr int kModeRetry = 3;   // branch: history dropped, direction -g
-struct __align__(8) SolveState {
+struct __align__(16) SolveState {  // 16-byte aligned: copied to shared memory with 16-byte vectors
   // configuration (set by the host before each launch)
   int64_t n;
   int m, max_iter, max_ls, max_evals;
@@ -378,13 +378,12 @@ cudaError_t launch_axpy(const double* x, double a, const double* d, double* out,
 
 // Device-resident level solve (k_solve.cu; the line-search decision itself
 // runs in the regulariser kernel, solve.cuh).
-cudaError_t launch_solve_trial(const SolveState* S, const double* x, const double* dir, double* xt, int64_t n,
-                               cudaStream_t s);
-cudaError_t launch_solve_post_trial(const SolveState* S, double* xt, double* gt, double* xb, double* gb, int64_t n,
-                                    cudaStream_t s);
-cudaError_t launch_solve_pair(const SolveState* S, const HistSet& H, const double* xt, const double* gt, double* x,
-                              double* g, int64_t n, cudaStream_t s);
+cudaError_t launch_solve_trial(const SolveState* S, const double* x, const double* dir, double* xt, const double* gt,
+                               double* xb, double* gb, int64_t n, cudaStream_t s);
+cudaError_t launch_solve_pair(const SolveState* S, const HistSet& H, const double* xt, const double* gt,
+                              const double* xb, const double* gb, double* x, double* g, int64_t n, cudaStream_t s);
 int solve_dots_blocks(int64_t n);
+int device_sm_count();  // SMs of the current device (queried once per device)
 cudaError_t launch_solve_dots(SolveState* S, const HistSet& H, int m, const double* g, int64_t n, double* partials,
                               unsigned* counter, cudaStream_t s);
 cudaError_t launch_solve_comb(const SolveState* S, const HistSet& H, const double* g, double* dir, int64_t n,

@@ -19,10 +19,8 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kChunk = 20;             // history vectors per block row
-constexpr int kPerThread = 8;          // elements per thread on long vectors
-constexpr int kMinBlocks = 152;        // blocks per row: at least one per SM
-constexpr int kMaxBlocks = 8 * 152;    // blocks per row
 constexpr int kMaxVec = 2 * kMaxM + 2; // history vectors of one product pass
+constexpr int kVals = 64;              // per-thread partial sums of the products (2 kChunk + 2, padded)
 
 __device__ __forceinline__ unsigned long long abs_bits(double v) {
   return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
@@ -32,44 +30,45 @@ __device__ __forceinline__ const double* hvec(const HistSet& H, int id) {
   return (id & 1) ? H.Y[id >> 1] : H.S[id >> 1];
 }
 
-// xt = x + a dir (the start point itself in the init mode)
+// xt = x + a dir (the start point itself in the init mode).  First, if the
+// previous trial was kept as the line search's best Armijo point (and the
+// search goes on), it is saved to xb, gb before xt is overwritten (gt is
+// overwritten by the evaluation that follows).
 __global__ void __launch_bounds__(kThreads) trial_kernel(const SolveState* __restrict__ S, const double* __restrict__ x,
-                                                         const double* __restrict__ dir, double* __restrict__ xt,
-                                                         int64_t n) {
+                                                         const double* __restrict__ dir, double* xt,
+                                                         const double* __restrict__ gt, double* __restrict__ xb,
+                                                         double* __restrict__ gb, int64_t n) {
   const bool init = S->mode == kModeInit;
+  const bool save = S->save_best && !S->branch;
   const double a = S->a;
-  for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < n; e += (int64_t)gridDim.x * kThreads)
-    xt[e] = init ? x[e] : fma(a, dir[e], x[e]);
-}
-
-// keeps the trial as the best Armijo point, or puts the best point back as the trial
-__global__ void __launch_bounds__(kThreads) post_trial_kernel(const SolveState* __restrict__ S, double* xt, double* gt,
-                                                              double* xb, double* gb, int64_t n) {
-  const int save = S->save_best, restore = S->restore_best;
-  if (!save && !restore) return;
   for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < n; e += (int64_t)gridDim.x * kThreads) {
     if (save) {
       xb[e] = xt[e];
       gb[e] = gt[e];
-    } else {
-      xt[e] = xb[e];
-      gt[e] = gb[e];
     }
+    xt[e] = init ? x[e] : fma(a, dir[e], x[e]);
   }
 }
 
 // accepted step: s = xt - x and y = gt - g into the spare buffers; the trial
-// becomes the iterate (also in the init mode); nothing in the retry mode
+// becomes the iterate (also in the init mode); nothing in the retry mode.
+// When the line search ended on its best Armijo point rather than on the last
+// trial, that point (xb, gb) is taken instead -- unless the last trial is
+// itself that point (kept and taken by the same decision).
 __global__ void __launch_bounds__(kThreads) pair_kernel(const SolveState* __restrict__ S, const HistSet H,
                                                         const double* __restrict__ xt, const double* __restrict__ gt,
+                                                        const double* __restrict__ xb, const double* __restrict__ gb,
                                                         double* __restrict__ x, double* __restrict__ g, int64_t n) {
   const int mode = S->mode;
   if (mode == kModeRetry) return;
+  const bool best = S->restore_best && !S->save_best;
+  const double* xs = best ? xb : xt;
+  const double* gs = best ? gb : gt;
   double* sv = H.S[S->spare];
   double* yv = H.Y[S->spare];
   const bool pair = mode == kModeAccept;
   for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < n; e += (int64_t)gridDim.x * kThreads) {
-    const double xn = xt[e], gn = gt[e];
+    const double xn = xs[e], gn = gs[e];
     if (pair) {
       sv[e] = xn - x[e];
       yv[e] = gn - g[e];
@@ -127,6 +126,27 @@ __device__ void history_update(SolveState* S) {
   S->gmax = r[2 * K + 2];
 }
 
+// Block-wide copy of the solver state, 16 bytes per load, all of a thread's
+// loads issued before its stores.
+__device__ __forceinline__ void copy_state(SolveState* dst, const SolveState* src) {
+  constexpr int kWords = (int)(sizeof(SolveState) / 16);
+  constexpr int kPer = (kWords + kThreads - 1) / kThreads;
+  const int4* s4 = reinterpret_cast<const int4*>(src);
+  int4* d4 = reinterpret_cast<int4*>(dst);
+  int4 buf[kPer];
+#pragma unroll
+  for (int i = 0; i < kPer; i++) {
+    const int w = threadIdx.x + i * kThreads;
+    if (w < kWords) buf[i] = s4[w];
+  }
+#pragma unroll
+  for (int i = 0; i < kPer; i++) {
+    const int w = threadIdx.x + i * kThreads;
+    if (w < kWords) d4[w] = buf[i];
+  }
+}
+static_assert(sizeof(SolveState) % 16 == 0, "solver state is copied in 16-byte words");
+
 // After the products: history update, stopping tests, and the compact-form
 // (Byrd, Nocedal & Schnabel) direction dir = -H g with H0 = gamma I, gamma
 // from the newest pair, as coefficients of g and the history vectors; g . dir
@@ -139,6 +159,7 @@ struct Algebra {
   double R[kMaxM][kMaxM];   // R_ij = s_i . y_j
   double YY[kMaxM][kMaxM];  // y_i . y_j
   double a[kMaxM], b[kMaxM], u[kMaxM], w[kMaxM], top[kMaxM];
+  double rd[kMaxM];         // 1 / R_ii
   int proceed;
 };
 
@@ -172,6 +193,8 @@ __device__ void after_products(SolveState* S, Algebra& A) {
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
     A.a[i] = S->sg[S->order[i]];
     A.b[i] = S->yg[S->order[i]];
+    // the divisions (long float64 sequences) off the serial solves below
+    A.rd[i] = 1.0 / SYa(S, S->order[i], S->order[i]);
   }
   __syncthreads();
   double gamma = 0.0;
@@ -180,7 +203,7 @@ __device__ void after_products(SolveState* S, Algebra& A) {
     for (int i = k - 1; i >= 0; i--) {
       double s = A.a[i];
       for (int j = i + 1; j < k; j++) s -= A.R[i][j] * A.u[j];
-      A.u[i] = s / A.R[i][i];
+      A.u[i] = s * A.rd[i];
     }
   }
   __syncthreads();
@@ -196,7 +219,7 @@ __device__ void after_products(SolveState* S, Algebra& A) {
     for (int i = 0; i < k; i++) {  // top = R^{-T} w
       double s = A.w[i];
       for (int j = 0; j < i; j++) s -= A.R[j][i] * A.top[j];
-      A.top[i] = s / A.R[i][i];
+      A.top[i] = s * A.rd[i];
     }
     S->cg = -gamma;
     S->nc = 0;
@@ -228,16 +251,70 @@ __device__ void after_products(SolveState* S, Algebra& A) {
   S->mode = kModeTrial;
 }
 
+// Reduce-scatter of 32 per-lane float64 values over the warp: on return v[0]
+// of lane i is the warp total of value i.  Each stage keeps half of the
+// values and adds the partner lane's copy of that half, so a lane does 31
+// float64 adds for 32 values (a butterfly per value would do 160, and this
+// GPU runs float64 at 1/64 of the float rate).  The pairing is fixed, so the
+// sums are reproducible.
+template <int N>
+__device__ __forceinline__ void rs_stage(double* v, int lane) {
+  const bool up = (lane & N) != 0;
+#pragma unroll
+  for (int j = 0; j < N; j++) {
+    const double send = up ? v[j] : v[j + N];
+    const double keep = up ? v[j + N] : v[j];
+    v[j] = keep + __shfl_xor_sync(0xffffffffu, send, N);
+  }
+}
+
+__device__ __forceinline__ double warp_reduce_scatter32(double* v, int lane) {
+  rs_stage<16>(v, lane);
+  rs_stage<8>(v, lane);
+  rs_stage<4>(v, lane);
+  rs_stage<2>(v, lane);
+  rs_stage<1>(v, lane);
+  return v[0];
+}
+
+// The products pass over this block's share of the elements: v[2c] += h_c
+// q0 (accepted step only), v[2c+1] += h_c g; v[2 kChunk], v[2 kChunk + 1]:
+// q0 . q0 and g . g (first row only); mx: max |g| as ordered bits.
+template <bool kAccepted>
+__device__ __forceinline__ void dots_pass(const double* const* h, int kn, bool first, const double* __restrict__ q0,
+                                          const double* __restrict__ g, int64_t e0, int64_t e1, double* v,
+                                          unsigned long long& mx) {
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += kThreads) {
+    const double gv = g[e];
+    const double v0 = kAccepted ? q0[e] : 0.0;
+#pragma unroll
+    for (int c = 0; c < kChunk; c++) {
+      if (c < kn) {
+        const double hv = h[c][e];
+        if (kAccepted) v[2 * c] = fma(hv, v0, v[2 * c]);
+        v[2 * c + 1] = fma(hv, gv, v[2 * c + 1]);
+      }
+    }
+    if (first) {
+      if (kAccepted) v[2 * kChunk] = fma(v0, v0, v[2 * kChunk]);
+      v[2 * kChunk + 1] = fma(gv, gv, v[2 * kChunk + 1]);
+      mx = max(mx, abs_bits(gv));
+    }
+  }
+}
+
 // Products of the candidate history vectors (the stored pairs and, after an
 // accepted step, the new one) with the probes y_new (accepted step only) and
-// g; g . g and max|g|.  Grid (G, rows), rows enough for the problem's
-// longest history: block (bx, r) takes candidates r*20 .. r*20+19 over a
-// strided share of the elements (rows beyond this step's candidates only
-// arrive); the last block to finish adds the block partials (fixed trees)
-// and runs the algebra.
-__global__ void __launch_bounds__(kThreads, 2) dots_kernel(SolveState* S, const HistSet H, const double* __restrict__ g,
-                                                        int64_t n, double* partials, unsigned* counter) {
-  __shared__ double sm[(2 * kChunk + 3) * kWarps];
+// g; g . g and max|g|.  Grid (G, rows): G blocks (one per SM) split the
+// elements into contiguous shares, rows cover the problem's longest history
+// (block (bx, r) takes candidates r*20 .. r*20+19; rows beyond this step's
+// candidates only arrive).  Within a block the float64 partial sums go
+// through the reduce-scatter above and a fixed sum over the warps; the last
+// block to finish adds the block partials (fixed order) and runs the algebra.
+__global__ void __launch_bounds__(kThreads, 1) dots_kernel(SolveState* S, const HistSet H, const double* __restrict__ g,
+                                                           int64_t n, double* partials, unsigned* counter) {
+  __shared__ double sm[kVals * kWarps];
+  __shared__ unsigned long long smx[kWarps];
   __shared__ bool is_last;
   const int G = gridDim.x;
   const bool accepted = S->mode == kModeAccept;
@@ -247,13 +324,13 @@ __global__ void __launch_bounds__(kThreads, 2) dots_kernel(SolveState* S, const 
   const int k0 = blockIdx.y * kChunk;
   const int kn = min(kChunk, K - k0);
   const bool first = blockIdx.y == 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (kn <= 0 && !first) {  // a row beyond this step's vectors: only arrive
     __syncthreads();
     if (threadIdx.x == 0) is_last = (atomicAdd(counter, 1u) == gridDim.x * gridDim.y - 1);
     __syncthreads();
     if (!is_last) return;
   } else {
-  const double* q0 = accepted ? H.Y[S->spare] : nullptr;
   const double* h[kChunk];
 #pragma unroll
   for (int c = 0; c < kChunk; c++) {
@@ -265,69 +342,42 @@ __global__ void __launch_bounds__(kThreads, 2) dots_kernel(SolveState* S, const 
       h[c] = (v & 1) ? H.Y[buf] : H.S[buf];
     }
   }
-  double a0[kChunk], a1[kChunk];
+  // contiguous share of the elements, a multiple of 32 long (coalesced)
+  const int64_t share = ((n + G - 1) / G + 31) / 32 * 32;
+  const int64_t e0 = min(n, (int64_t)blockIdx.x * share), e1 = min(n, e0 + share);
+  double v[kVals];
 #pragma unroll
-  for (int c = 0; c < kChunk; c++) a0[c] = a1[c] = 0.0;
-  double qq0 = 0.0, qq1 = 0.0;
+  for (int c = 0; c < kVals; c++) v[c] = 0.0;
   unsigned long long mx = 0ull;
-  for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < n; e += (int64_t)G * kThreads) {
-    const double v0 = q0 ? q0[e] : 0.0;
-    const double gv = g[e];
-#pragma unroll
-    for (int c = 0; c < kChunk; c++) {
-      if (c < kn) {
-        const double hv = h[c][e];
-        a0[c] = fma(hv, v0, a0[c]);
-        a1[c] = fma(hv, gv, a1[c]);
-      }
-    }
-    if (first) {
-      qq0 = fma(v0, v0, qq0);
-      qq1 = fma(gv, gv, qq1);
-      mx = max(mx, abs_bits(gv));
-    }
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int c = 0; c < kChunk; c++) {
-    if (c < kn) {
-      double u0 = warp_sum(a0[c]), u1 = warp_sum(a1[c]);
-      if (lane == 0) {
-        sm[(2 * c) * kWarps + warp] = u0;
-        sm[(2 * c + 1) * kWarps + warp] = u1;
-      }
-    }
-  }
+  if (accepted) dots_pass<true>(h, kn, first, H.Y[S->spare], g, e0, e1, v, mx);
+  else dots_pass<false>(h, kn, first, nullptr, g, e0, e1, v, mx);
+  // warp totals: lane i holds values i and 32 + i
+  const double t0 = warp_reduce_scatter32(v, lane);
+  const double t1 = warp_reduce_scatter32(v + 32, lane);
+  sm[lane * kWarps + warp] = t0;
+  sm[(32 + lane) * kWarps + warp] = t1;
   if (first) {
-    qq0 = warp_sum(qq0);
-    qq1 = warp_sum(qq1);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) {
-      sm[(2 * kChunk) * kWarps + warp] = qq0;
-      sm[(2 * kChunk + 1) * kWarps + warp] = qq1;
-      sm[(2 * kChunk + 2) * kWarps + warp] = __longlong_as_double((long long)mx);
-    }
+    if (lane == 0) smx[warp] = mx;
   }
   __syncthreads();
-  // outputs: [2v] = h_v . q0, [2v+1] = h_v . g, [2K] = q0 . q0, [2K+1] = g . g, [2K+2] = max|g|
-  const int nloc = 2 * max(kn, 0);
-  for (int t = threadIdx.x; t < 2 * kChunk + 3; t += kThreads) {
-    if (t < nloc) {
-      double v = 0.0;
-      for (int w = 0; w < kWarps; w++) v += sm[t * kWarps + w];
-      partials[(int64_t)(2 * k0 + t) * G + blockIdx.x] = v;
-    } else if (first && t >= 2 * kChunk) {
-      const int x = t - 2 * kChunk;
-      double v = 0.0;
-      unsigned long long m = 0ull;
-      for (int w = 0; w < kWarps; w++) {
-        const double u = sm[t * kWarps + w];
-        if (x == 2) m = max(m, (unsigned long long)__double_as_longlong(u));
-        else v += u;
-      }
-      partials[(int64_t)(2 * K + x) * G + blockIdx.x] = (x == 2) ? __longlong_as_double((long long)m) : v;
-    }
+  // block partials, outputs: [2v] = h_v . q0, [2v+1] = h_v . g, [2K] = q0 . q0,
+  // [2K+1] = g . g, [2K+2] = max|g|
+  const int t = threadIdx.x;
+  int out = -1;
+  if (t < 2 * kn) out = 2 * k0 + t;
+  else if (first && t == 2 * kChunk) out = 2 * K;
+  else if (first && t == 2 * kChunk + 1) out = 2 * K + 1;
+  if (out >= 0) {
+    double a = 0.0;
+    for (int w = 0; w < kWarps; w++) a += sm[t * kWarps + w];
+    partials[(int64_t)out * G + blockIdx.x] = a;
+  }
+  if (first && t == kThreads - 1) {
+    unsigned long long m = 0ull;
+    for (int w = 0; w < kWarps; w++) m = max(m, smx[w]);
+    partials[(int64_t)(2 * K + 2) * G + blockIdx.x] = __longlong_as_double((long long)m);
   }
   __threadfence();
   __syncthreads();
@@ -339,43 +389,34 @@ __global__ void __launch_bounds__(kThreads, 2) dots_kernel(SolveState* S, const 
   // the epilogue works on a shared-memory copy of the state: its serial parts
   // would otherwise wait on L2 for every dependent access
   __shared__ SolveState sS;
-  {
-    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(S);
-    unsigned long long* dst = reinterpret_cast<unsigned long long*>(&sS);
-    for (int t = threadIdx.x; t < (int)(sizeof(SolveState) / 8); t += kThreads) dst[t] = src[t];
-  }
+  copy_state(&sS, S);
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nout = 2 * K + 3;
   for (int o = warp; o < nout; o += kWarps) {
     const bool is_max = (o == nout - 1);
-    double v = 0.0;
+    double a = 0.0;
     unsigned long long m = 0ull;
     for (int bx = lane; bx < G; bx += 32) {
       const double u = partials[(int64_t)o * G + bx];
       if (is_max) m = max(m, (unsigned long long)__double_as_longlong(u));
-      else v += u;
+      else a += u;
     }
-    v = warp_sum(v);
+    a = warp_sum(a);
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, s));
-    if (lane == 0) sS.dots[o] = is_max ? __longlong_as_double((long long)m) : v;
+    if (lane == 0) sS.dots[o] = is_max ? __longlong_as_double((long long)m) : a;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     *counter = 0u;
     sS.ncand = ncand;
-    for (int t = 0; t < ncand; t++) sS.cand[t] = (t < nstored) ? sS.order[t] : sS.spare;
+    for (int c = 0; c < ncand; c++) sS.cand[c] = (c < nstored) ? sS.order[c] : sS.spare;
   }
   __syncthreads();
   __shared__ Algebra alg;
   after_products(&sS, alg);
   __syncthreads();
-  {
-    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&sS);
-    unsigned long long* dst = reinterpret_cast<unsigned long long*>(S);
-    for (int t = threadIdx.x; t < (int)(sizeof(SolveState) / 8); t += kThreads) dst[t] = src[t];
-  }
+  copy_state(S, &sS);
 }
 
 // dir = cg g + sum_j coef_j h_j (float64, terms in a fixed order)
@@ -462,30 +503,36 @@ inline unsigned grid_for(int64_t n) {
 }  // namespace
 
 // The products are float64 work, which this GPU runs at 1/64 of the float
-// rate per SM: every SM takes a share (at least one block each), with about
-// kPerThread elements per thread on long vectors.
+// rate per SM: one block per SM, each with a contiguous share of the
+// elements (fewer blocks on short vectors).
 int solve_dots_blocks(int64_t n) {
-  int64_t b = (n + (int64_t)kThreads * kPerThread - 1) / ((int64_t)kThreads * kPerThread);
-  if (b < kMinBlocks) b = kMinBlocks;
-  if (b > kMaxBlocks) b = kMaxBlocks;
+  int64_t b = (n + kThreads - 1) / kThreads;
+  const int sms = device_sm_count();
+  if (b > sms) b = sms;
+  if (b < 1) b = 1;
   return (int)b;
 }
 
-cudaError_t launch_solve_trial(const SolveState* S, const double* x, const double* dir, double* xt, int64_t n,
-                               cudaStream_t s) {
-  trial_kernel<<<grid_for(n), kThreads, 0, s>>>(S, x, dir, xt, n);
+int device_sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 152;
+  if (dev < 64 && cached[dev] > 0) return cached[dev];
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+  if (dev < 64) cached[dev] = sms;
+  return sms;
+}
+
+cudaError_t launch_solve_trial(const SolveState* S, const double* x, const double* dir, double* xt, const double* gt,
+                               double* xb, double* gb, int64_t n, cudaStream_t s) {
+  trial_kernel<<<grid_for(n), kThreads, 0, s>>>(S, x, dir, xt, gt, xb, gb, n);
   return cudaGetLastError();
 }
 
-cudaError_t launch_solve_post_trial(const SolveState* S, double* xt, double* gt, double* xb, double* gb, int64_t n,
-                                    cudaStream_t s) {
-  post_trial_kernel<<<grid_for(n), kThreads, 0, s>>>(S, xt, gt, xb, gb, n);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_solve_pair(const SolveState* S, const HistSet& H, const double* xt, const double* gt, double* x,
-                              double* g, int64_t n, cudaStream_t s) {
-  pair_kernel<<<grid_for(n), kThreads, 0, s>>>(S, H, xt, gt, x, g, n);
+cudaError_t launch_solve_pair(const SolveState* S, const HistSet& H, const double* xt, const double* gt,
+                              const double* xb, const double* gb, double* x, double* g, int64_t n, cudaStream_t s) {
+  pair_kernel<<<grid_for(n), kThreads, 0, s>>>(S, H, xt, gt, xb, gb, x, g, n);
   return cudaGetLastError();
 }
 
