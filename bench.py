@@ -4,11 +4,14 @@ the converged coarse-to-fine solve per pair with its accuracy.
 
 A step is one objective + gradient evaluation at full resolution through the
 library (displacement -> data term + regulariser + mean term + final
-reductions, f read back on the host), at the pair's true displacement plus
-0.5 px of Gaussian noise (the same evaluation at the true field is reported
-beside it).  ``value`` times steps with inputs resident in GPU memory;
-``e2e`` times the same call with the displacement copied in from pinned host
-memory and the gradient copied back every step.  The two volumes (368 MB)
+reductions, the result terms written to device memory), at the pair's true
+displacement plus 0.5 px of Gaussian noise (the same evaluation at the true
+field is reported beside it).  ``value`` times steps issued back to back
+through the asynchronous entry point with inputs resident in GPU memory (as
+the device-resident solver consumes evaluations); ``sync_api`` times the
+synchronous call, which reads f back on the host every step; ``e2e`` times
+that call with the displacement copied in from pinned host memory and the
+gradient copied back every step.  The two volumes (368 MB)
 exceed the 129 MB L2, so every step streams them from HBM.
 
 The solve runs every level to the library's stopping rule (one device
@@ -383,6 +386,22 @@ def time_evals(P, D, G, steps, stream, barrier, profile=True):
     return ms, kern
 
 
+def time_evals_async(P, D, G, T, steps, stream, barrier):
+    """ms for `steps` evaluations enqueued back to back on `stream` (result
+    terms to the device buffer T), one synchronisation at the end."""
+    for _ in range(3):
+        P.eval_objective_grad_async(0, D, G, T, stream)
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(steps):
+        P.eval_objective_grad_async(0, D, G, T, stream)
+    e1.record(stream)
+    barrier()
+    return e0.elapsed_time(e1)
+
+
 def run_ours(args):
     import torch
     dist, rank, ws = dist_setup(args)
@@ -415,8 +434,11 @@ def run_ours(args):
     t_soak = time.perf_counter()
     while time.perf_counter() - t_soak < 1.0:
         P.eval_objective_grad(0, D, G)
-    ms, kern_ms = time_evals(P, D, G, args.steps, stream, barrier)
-    ms_truth, kern_truth = time_evals(P, Dt, G, args.steps, stream, barrier)
+    ms_sync, kern_ms = time_evals(P, D, G, args.steps, stream, barrier)
+    ms_truth_sync, kern_truth = time_evals(P, Dt, G, args.steps, stream, barrier)
+    T = torch.zeros(6, dtype=torch.float64, device="cuda")
+    ms = time_evals_async(P, D, G, T, args.steps, stream, barrier)
+    ms_truth = time_evals_async(P, Dt, G, T, args.steps, stream, barrier)
 
     # ---- end to end through host buffers
     Dh = D.cpu().pin_memory()
@@ -560,6 +582,9 @@ def run_ours(args):
                      "peak_note": "alu peak derived: %d SMs (queried) x 128 FP32 lanes x 2 flop x %.0f MHz; "
                                   "hbm peak of measured" % (nsm, sm_max)},
         "at_true_field": {"evals_per_s": args.steps / (ms_truth / 1e3), "data_kernel_ms": kern_truth},
+        "sync_api": {"evals_per_s": args.steps / (ms_sync / 1e3),
+                     "at_true_field_evals_per_s": args.steps / (ms_truth_sync / 1e3),
+                     "note": "octmc_eval_objective_grad: f read back on the host every step"},
         "e2e": {"value": replica_value(ws, args.steps, ms_e2e), "unit": "evals/s",
                 "h2d_bytes_per_step": int(Dh.numel() * 8), "d2h_bytes_per_step": int(Gh.numel() * 8)},
         "gpu_launches": 3 * args.steps,

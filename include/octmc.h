@@ -132,6 +132,18 @@ int octmc_compute_eta(octmc_problem *p, int level, const double *disp0_dev, doub
 int octmc_eval_objective_grad(octmc_problem *p, int level, const double *disp_dev, double *f_host,
                               double *grad_dev);
 
+/* octmc_eval_objective_grad enqueued on `stream` (a cudaStream_t; NULL: the
+ * problem's own stream) without waiting for it: the host is not
+ * synchronised and no result comes back to the host.  terms_dev (device, may
+ * be NULL) receives [S^str, S^ang, R, M, f, eta] as 6 doubles when the
+ * evaluation completes in stream order; grad_dev as for the synchronous call.
+ * Consecutive calls on one stream may reuse the problem's scratch buffers;
+ * calls on one problem must not be issued on two streams at once.  A
+ * non-finite f is not reported here (terms_dev holds it).  Errors:
+ * INVALID_ARG, CUDA (a launch failed). */
+int octmc_eval_objective_grad_async(octmc_problem *p, int level, const double *disp_dev, double *grad_dev,
+                                    double *terms_dev, void *stream);
+
 /* As octmc_eval_objective_grad, and terms_host[6] receives
  * [S^str, S^ang, R, M, f, eta] (Eq. 5, Eq. 6, R, M, f, eta). */
 int octmc_eval_terms(octmc_problem *p, int level, const double *disp_dev, double *terms_host,

@@ -134,6 +134,22 @@ class Problem:
                 "octmc_eval_objective_grad")
         return f.value
 
+    def eval_objective_grad_async(self, level, disp, grad=None, terms=None, stream=None):
+        """Enqueues the evaluation on ``stream`` (a torch.cuda.Stream; default:
+        the current stream) and returns at once.  ``terms`` (float64 CUDA
+        tensor of 6, optional) receives [S^str, S^ang, R, M, f, eta] in stream
+        order; ``grad`` as for eval_objective_grad."""
+        _check_disp(disp, self.disp_shape(level))
+        if grad is not None:
+            _check_disp(grad, self.disp_shape(level))
+        if terms is not None and (terms.dtype != torch.float64 or not terms.is_cuda or terms.numel() < 6
+                                  or not terms.is_contiguous()):
+            raise ValueError("terms must be a contiguous float64 CUDA tensor of at least 6 values")
+        st = stream if stream is not None else torch.cuda.current_stream()
+        N.check(N.lib().octmc_eval_objective_grad_async(self._h, level, _ptr(disp), _ptr(grad), _ptr(terms),
+                                                        C.c_void_p(st.cuda_stream)),
+                "octmc_eval_objective_grad_async")
+
     def eval_terms(self, level, disp, grad=None):
         """[S^str, S^ang, R, M, f, eta] as a numpy array; optional gradient as above."""
         _check_disp(disp, self.disp_shape(level))

@@ -49,6 +49,8 @@ _SIGS = {
     "octmc_eval_objective_grad": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_double),
                                             C.c_void_p]),
     "octmc_eval_terms": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
+    "octmc_eval_objective_grad_async": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                                  C.c_void_p]),
     "octmc_eval_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_void_p),
                                    C.POINTER(C.c_void_p), C.POINTER(C.c_double)]),
     "octmc_solve_level": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(Stats)]),

@@ -557,6 +557,8 @@ struct EvalReq {
   const double* dir;  // null: no grad . dir
   double eta;
   double delta0;
+  bool async = false;           // no host copy of the result (the caller does not wait)
+  double* terms_dev = nullptr;  // if set: the 6 result terms copied here (device)
 };
 
 // A non-blocking side stream with its fork/join events, one per thread and
@@ -646,7 +648,7 @@ void eval_batch(cudaStream_t st, const std::vector<EvalReq>& reqs) {
     CK(launch_msum_multi(MM, ss.s));
     CK(cudaEventRecord(ss.join, ss.s));
     octmc_problem* P0 = reqs[c0].P;
-    const bool prof = (ns == 1 && P0->profile);
+    const bool prof = (ns == 1 && P0->profile && !reqs[c0].async);
     if (prof) CK(cudaEventRecord(P0->ev0, st));
     for (int dt = 0; dt < 3; dt++) {
       if (!nd[dt]) continue;
@@ -660,8 +662,10 @@ void eval_batch(cudaStream_t st, const std::vector<EvalReq>& reqs) {
     CK(cudaStreamWaitEvent(st, ss.join, 0));
     CK(launch_reg_multi(RM, st));
     for (int k = 0; k < ns; k++) {
-      octmc_problem* P = reqs[c0 + k].P;
-      CK(cudaMemcpyAsync(P->res_host, P->res, sizeof(EvalResult), cudaMemcpyDeviceToHost, st));
+      const EvalReq& q = reqs[c0 + k];
+      if (q.terms_dev)
+        CK(cudaMemcpyAsync(q.terms_dev, q.P->res->terms, sizeof(double) * 6, cudaMemcpyDeviceToDevice, st));
+      if (!q.async) CK(cudaMemcpyAsync(q.P->res_host, q.P->res, sizeof(EvalResult), cudaMemcpyDeviceToHost, st));
     }
   }
 }
@@ -1345,6 +1349,20 @@ int octmc_eval_objective_grad(octmc_problem* p, int level, const double* disp, d
   const int rc = octmc_eval_terms(p, level, disp, terms, grad);
   if (f && (rc == OCTMC_OK || rc == OCTMC_ERR_NONFINITE)) *f = terms[4];
   return rc;
+}
+
+int octmc_eval_objective_grad_async(octmc_problem* p, int level, const double* disp, double* grad,
+                                    double* terms_dev, void* stream) {
+  if (!valid_level(p, level) || !disp) return OCTMC_ERR_INVALID_ARG;
+  return guarded([&] {
+    const cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : p->st;
+    EvalReq q{p, level, disp, grad, nullptr, p->lv[level].eta, p->desc.delta0};
+    q.async = true;
+    q.terms_dev = terms_dev;
+    eval_batch(st, std::vector<EvalReq>{q});
+    CK(cudaGetLastError());
+    return OCTMC_OK;
+  });
 }
 
 int octmc_eval_batch(octmc_problem* const* problems, int count, const int* levels, const double* const* disp,

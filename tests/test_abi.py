@@ -50,6 +50,7 @@ def test_host_only_calls(lib_path):
     assert L.octmc_create_problem(None, ctypes.byref(h)) == -1
     assert L.octmc_create_problem(ctypes.byref(d), ctypes.byref(h)) == -1  # w = h = d = 0
     assert L.octmc_level_shape(None, 0, None, None, None) == -1
+    assert L.octmc_eval_objective_grad_async(None, 0, None, None, None, None) == -1
     assert L.octmc_lbfgs_create(0, 8, None, ctypes.byref(h)) == -1
     # history length 1..32: the dot-product kernel holds 2 (m + 1) <= 66 history vectors
     assert L.octmc_lbfgs_create(100, 0, None, ctypes.byref(h)) == -1

@@ -391,3 +391,30 @@ def test_solve_full_converged_minimum_clinical_size(c2):
     assert f_g <= f_o * (1.0 + 1e-3)
     assert med <= 0.05
     assert rms <= 0.5
+
+
+def test_async_evaluation_equals_the_synchronous_one(c1):
+    # the same evaluation enqueued without waiting, back to back on one
+    # stream: bitwise the synchronous result, the terms left in device memory
+    p, cfg = c1
+    G = gpu_problem(p)
+    G.set_eta(0, 0.8)
+    rng = np.random.default_rng(11)
+    Ds = [cuda(rng.normal(0.0, 0.7, G.disp_shape(0))) for _ in range(3)]
+    ref = []
+    for D in Ds:
+        g = torch.zeros(G.disp_shape(0), dtype=torch.float64, device="cuda")
+        t = G.eval_terms(0, D, g)
+        ref.append((t, g))
+    st = torch.cuda.Stream()
+    outs = []
+    with torch.cuda.stream(st):
+        for D in Ds:
+            g = torch.zeros(G.disp_shape(0), dtype=torch.float64, device="cuda")
+            t = torch.zeros(6, dtype=torch.float64, device="cuda")
+            G.eval_objective_grad_async(0, D, g, t, stream=st)
+            outs.append((t, g))
+    st.synchronize()
+    for (t, g), (tr, gr) in zip(outs, ref):
+        assert np.array_equal(t.cpu().numpy(), np.asarray(tr, dtype=np.float64))
+        assert torch.equal(g, gr)
