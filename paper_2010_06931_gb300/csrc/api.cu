@@ -765,15 +765,19 @@ cudaGraphNode_t capture_after(octmc_problem* P, cudaGraph_t g, cudaGraphNode_t d
 }
 
 // msum (side stream) + data + reg at the level's current x or trial point
+// With ctl (inside a level's loop) the mean-term sums are not launched here:
+// the trial kernel forms them with the trial point.
 void capture_eval(octmc_problem* P, cudaStream_t cs, int l, const double* x, double* grad, const double* dir,
                   double eta, const double* eta_dev, double delta0, SolveState* ctl,
-                  cudaGraphConditionalHandle hb) {
+                  cudaGraphConditionalHandle hb, cudaGraphConditionalHandle hw) {
   const Level& Lv = P->lv[l];
   const int64_t plane = P->plane(l);
-  CK(cudaEventRecord(P->cap_fork, cs));
-  CK(cudaStreamWaitEvent(P->cap_side, P->cap_fork, 0));
-  CK(launch_msum(x, plane, P->res, P->partials, P->counters + 0, P->cap_side));
-  CK(cudaEventRecord(P->cap_join, P->cap_side));
+  if (!ctl) {
+    CK(cudaEventRecord(P->cap_fork, cs));
+    CK(cudaStreamWaitEvent(P->cap_side, P->cap_fork, 0));
+    CK(launch_msum(x, plane, P->res, P->partials, P->counters + 0, P->cap_side));
+    CK(cudaEventRecord(P->cap_join, P->cap_side));
+  }
   DataArgs A;
   std::memset(&A, 0, sizeof(A));
   A.L = Lv.dev;
@@ -787,7 +791,7 @@ void capture_eval(octmc_problem* P, cudaStream_t cs, int l, const double* x, dou
   A.eps_h = (float)P->desc.eps_h;
   A.loss = P->desc.loss;
   CK(launch_data(A, cs));
-  CK(cudaStreamWaitEvent(cs, P->cap_join, 0));
+  if (!ctl) CK(cudaStreamWaitEvent(cs, P->cap_join, 0));
   RegArgs R;
   std::memset(&R, 0, sizeof(R));
   R.L = Lv.dev;
@@ -807,6 +811,7 @@ void capture_eval(octmc_problem* P, cudaStream_t cs, int l, const double* x, dou
   R.counter = P->counters + 1;
   R.ctl = ctl;
   R.h_branch = hb;
+  R.h_while = hw;
   CK(launch_reg(R, cs));
 }
 
@@ -833,7 +838,7 @@ cudaGraphNode_t append_level(octmc_problem* P, cudaGraph_t g, cudaGraphNode_t de
   cfg.have_ang = P->have_ang ? 1 : 0;
   // start-field evaluation for eta, the level's state, a zero direction
   dep = capture_after(P, g, dep, [&](cudaStream_t cs) {
-    if (P->have_ang) capture_eval(P, cs, l, P->x, nullptr, nullptr, 1.0, nullptr, 0.5, nullptr, 0);
+    if (P->have_ang) capture_eval(P, cs, l, P->x, nullptr, nullptr, 1.0, nullptr, 0.5, nullptr, 0, 0);
     CK(launch_solve_level_init(S, P->res, cfg, cs));
     CK(cudaMemsetAsync(P->dir, 0, sizeof(double) * n, cs));
   });
@@ -850,9 +855,10 @@ cudaGraphNode_t append_level(octmc_problem* P, cudaGraph_t g, cudaGraphNode_t de
   cudaGraph_t body = wp.conditional.phGraph_out[0];
   CK(cudaGraphConditionalHandleCreate(&hb, body, 0, cudaGraphCondAssignDefault));
   const double* eta_dev = &S->eta;
+  SolveVecs V{P->x, P->g, P->xt, P->gt, P->xb, P->gb, P->dir, n, P->plane(l)};
   const cudaGraphNode_t sink = capture_after(P, body, nullptr, [&](cudaStream_t cs) {
-    CK(launch_solve_trial(S, P->x, P->dir, P->xt, P->gt, P->xb, P->gb, n, cs));
-    capture_eval(P, cs, l, P->xt, P->gt, P->dir, 1.0, eta_dev, D.delta0, S, hb);
+    CK(launch_solve_trial(S, H, V, P->res, P->partials, P->counters + 0, cs));
+    capture_eval(P, cs, l, P->xt, P->gt, P->dir, 1.0, eta_dev, D.delta0, S, hb, hw);
   });
   cudaGraphNodeParams ip{};
   ip.type = cudaGraphNodeTypeConditional;
@@ -862,13 +868,11 @@ cudaGraphNode_t append_level(octmc_problem* P, cudaGraph_t g, cudaGraphNode_t de
   cudaGraphNode_t inode;
   CK(cudaGraphAddNode(&inode, body, &sink, nullptr, 1, &ip));
   capture_after(P, ip.conditional.phGraph_out[0], nullptr, [&](cudaStream_t cs) {
-    CK(launch_solve_pair(S, H, P->xt, P->gt, P->xb, P->gb, P->x, P->g, n, cs));
-    CK(launch_solve_dots(S, H, m, P->g, n, P->spartials, P->scounter, cs));
-    CK(launch_solve_comb(S, H, P->g, P->dir, n, cs));
+    CK(launch_solve_dots(S, H, m, V, P->spartials, P->scounter, cs));
   });
-  capture_after(P, body, inode, [&](cudaStream_t cs) { CK(launch_solve_loop(S, hw, cs)); });
-  // the level's statistics
+  // the level's last iterate, and its statistics
   return capture_after(P, g, wnode, [&](cudaStream_t cs) {
+    CK(launch_solve_finish(S, V, cs));
     CK(launch_solve_level_stats(S, P->lstats + stats_slot, cs));
   });
 }

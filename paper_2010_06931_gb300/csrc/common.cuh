@@ -220,7 +220,9 @@ struct __align__(16) SolveState {  // 16-byte aligned: copied to shared memory w
   double gtol, ftol;
   // line-search controller
   int mode, done, status, iters, evals, small, retried, ls, have_lo, save_best, restore_best, branch;
+  int moved;                    // the last decision took a new iterate (init or accepted step)
   double f, ft, fb, dg0, a, lo, hi;
+  double gmaxb;                 // max |g| at the line search's best Armijo point
   double eta;                   // Eq. 10 at the level's start field
   unsigned long long t_start;   // %globaltimer at the level's start (ns)
   // history: buffer ids 0..m; order[0..k) oldest first; cand the vectors of the last products
@@ -275,6 +277,7 @@ struct RegArgs {
   unsigned* counter;      // zero-initialised, reset by the last block
   SolveState* ctl;        // may be null: the line-search decision of a device-resident solve
   cudaGraphConditionalHandle h_branch;  // set with ctl: runs the accepted-step branch
+  cudaGraphConditionalHandle h_while;   // set with ctl: continues the level's loop
 };
 
 // Batched evaluation of several problems ("slots") in one launch per
@@ -378,19 +381,21 @@ cudaError_t launch_axpy(const double* x, double a, const double* d, double* out,
 
 // Device-resident level solve (k_solve.cu; the line-search decision itself
 // runs in the regulariser kernel, solve.cuh).
-cudaError_t launch_solve_trial(const SolveState* S, const double* x, const double* dir, double* xt, const double* gt,
-                               double* xb, double* gb, int64_t n, cudaStream_t s);
-cudaError_t launch_solve_pair(const SolveState* S, const HistSet& H, const double* xt, const double* gt,
-                              const double* xb, const double* gb, double* x, double* g, int64_t n, cudaStream_t s);
+// The vectors of one level solve (device, n = 6 w h float64 each; plane = w h).
+struct SolveVecs {
+  double *x, *g;    // iterate and its gradient
+  double *xt, *gt;  // trial point and its gradient
+  double *xb, *gb;  // the line search's best Armijo point
+  double* dir;      // search direction
+  int64_t n, plane;
+};
+cudaError_t launch_solve_trial(SolveState* S, const HistSet& H, const SolveVecs& V, EvalResult* res, double* partials,
+                               unsigned* counter, cudaStream_t s);
+cudaError_t launch_solve_dots(SolveState* S, const HistSet& H, int m, const SolveVecs& V, double* partials,
+                              unsigned* counter, cudaStream_t s);
+cudaError_t launch_solve_finish(const SolveState* S, const SolveVecs& V, cudaStream_t s);
 int solve_dots_blocks(int64_t n);
 int device_sm_count();  // SMs of the current device (queried once per device)
-cudaError_t launch_solve_dots(SolveState* S, const HistSet& H, int m, const double* g, int64_t n, double* partials,
-                              unsigned* counter, cudaStream_t s);
-cudaError_t launch_solve_comb(const SolveState* S, const HistSet& H, const double* g, double* dir, int64_t n,
-                              cudaStream_t s);
-cudaError_t launch_solve_loop(const SolveState* S, cudaGraphConditionalHandle h_while, cudaStream_t s);
-// eta from the evaluation at the start field (delta_0 = 0.5, eta = 1) and the
-// level's initial state
 cudaError_t launch_solve_level_init(SolveState* S, const EvalResult* res, SolveCfg cfg, cudaStream_t s);
 cudaError_t launch_solve_level_stats(const SolveState* S, LevelStatsDev* out, cudaStream_t s);
 

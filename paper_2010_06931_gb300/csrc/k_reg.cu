@@ -54,6 +54,20 @@ __device__ void block_sum(double (&v)[N]) {
   __syncthreads();
 }
 
+// Maximum of v over the block, valid in thread 0.
+__device__ unsigned long long block_max(unsigned long long v) {
+  __shared__ unsigned long long sm[kWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (lane == 0) sm[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int w = 1; w < kWarps; w++) v = max(v, sm[w]);
+  __syncthreads();
+  return v;
+}
+
 // True in every thread of the last of nblk blocks to finish (partials visible).
 __device__ bool last_block(unsigned* counter, int nblk) {
   __shared__ bool is_last;
@@ -142,6 +156,7 @@ __device__ void reg_body(const RegArgs& A, int blk, int nblk) {
 #pragma unroll
   for (int c = 0; c < 3; c++) two_mu_s[c] = (float)(2.0 * A.mu * A.result->msum[c]);
   double v[4] = {0.0, 0.0, 0.0, 0.0};  // S^str, S^ang, R, grad . dir
+  unsigned long long gmx = 0ull;       // max |grad| as the bits of a non-negative float64
   // one work item per A-scan and scan (2 n items): the three components of
   // one volume's displacement; the A-scan's S^str, S^ang go with scan X
   for (int64_t e = (int64_t)blk * kThreads + threadIdx.x; e < 2 * n; e += (int64_t)nblk * kThreads) {
@@ -170,8 +185,10 @@ __device__ void reg_body(const RegArgs& A, int blk, int nblk) {
       if (A.grad) {
         const int64_t gi = (V * 3 + c) * n + p;
         const float g = A.gdata[gi] + fmaf(alpha_d, gr, two_mu_s[c]);
-        A.grad[gi] = widen_exact(g);
-        if (A.dir) gd = fma(widen_exact(g), A.dir[gi], gd);  // line-search product in float64
+        const double gw = widen_exact(g);
+        A.grad[gi] = gw;
+        if (A.dir) gd = fma(gw, A.dir[gi], gd);  // line-search product in float64
+        gmx = max(gmx, (unsigned long long)__double_as_longlong(gw) & 0x7fffffffffffffffull);
       }
     }
     if (V == 0) {
@@ -182,10 +199,17 @@ __device__ void reg_body(const RegArgs& A, int blk, int nblk) {
     v[3] += gd;
   }
   block_sum<4>(v);
-  if (threadIdx.x == 0)
+  gmx = block_max(gmx);
+  if (threadIdx.x == 0) {
     for (int c = 0; c < 4; c++) A.partials[blk * 4 + c] = v[c];
+    A.partials[4 * nblk + blk] = __longlong_as_double((long long)gmx);
+  }
   if (last_block(A.counter, nblk)) {
     sum_partials<4>(A.partials, nblk, v);
+    unsigned long long m = 0ull;
+    for (int b = threadIdx.x; b < nblk; b += kThreads)
+      m = max(m, (unsigned long long)__double_as_longlong(A.partials[4 * nblk + b]));
+    m = block_max(m);
     if (threadIdx.x == 0) {
       const double* ms = A.result->msum;
       const double M = A.mu * (ms[0] * ms[0] + ms[1] * ms[1] + ms[2] * ms[2]);
@@ -200,7 +224,7 @@ __device__ void reg_body(const RegArgs& A, int blk, int nblk) {
       res->terms[5] = eta;
       res->gdir = v[3];
       *A.counter = 0u;
-      if (A.ctl) ls_decide(A.ctl, res->terms[4], v[3], A.h_branch);
+      if (A.ctl) ls_decide(A.ctl, res->terms[4], v[3], __longlong_as_double((long long)m), A.h_branch, A.h_while);
     }
   }
 }

@@ -1,10 +1,13 @@
 // Kernels of the device-resident level solve (Ploner et al., Sec. 2.1:
-// "gradient-based L-BFGS solver"): the trial point, keeping or restoring
-// the line search's best point, the history pair of an accepted step, the
-// history products with the compact-form (Byrd, Nocedal & Schnabel)
-// direction, the direction itself and the loop condition.  All state lives
-// in one SolveState in device memory; the host launches one graph per
-// level and reads the state once at the end.
+// "gradient-based L-BFGS solver").  One loop iteration is four kernels: the
+// trial kernel (the direction and the iterate left by the last decision, the
+// trial point, the mean-term sums), the data and regulariser kernels of the
+// evaluation (the regulariser's last block takes the line-search decision
+// and the stopping tests), and, after a new iterate or a retry, the products
+// kernel (history pair, history products, compact-form (Byrd, Nocedal &
+// Schnabel) direction coefficients).  All state lives in one SolveState in
+// device memory; the host launches one graph per solve and reads the state
+// once at the end.
 //
 // The products and the small dense algebra are float64 with fixed
 // reduction trees and a fixed operation order, so a solve is reproducible
@@ -30,52 +33,125 @@ __device__ __forceinline__ const double* hvec(const HistSet& H, int id) {
   return (id & 1) ? H.Y[id >> 1] : H.S[id >> 1];
 }
 
-// xt = x + a dir (the start point itself in the init mode).  First, if the
-// previous trial was kept as the line search's best Armijo point (and the
-// search goes on), it is saved to xb, gb before xt is overwritten (gt is
-// overwritten by the evaluation that follows).
-__global__ void __launch_bounds__(kThreads) trial_kernel(const SolveState* __restrict__ S, const double* __restrict__ x,
-                                                         const double* __restrict__ dir, double* xt,
-                                                         const double* __restrict__ gt, double* __restrict__ xb,
-                                                         double* __restrict__ gb, int64_t n) {
+// Sum of v over the block, valid in thread 0 (fixed tree).
+__device__ double block_sum1(double v) {
+  __shared__ double sm[kWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) sm[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    v = 0.0;
+    for (int w = 0; w < kWarps; w++) v += sm[w];
+  }
+  __syncthreads();
+  return v;
+}
+
+// One trial point of the line search, after what the last decision left to
+// do (Sec. 2.1):
+//  - a new iterate (the start point or an accepted step): x <- xs, g <- gs,
+//    xs being the last trial, or the saved best Armijo point when the search
+//    ended on it (unless that point is the last trial itself);
+//  - the previous trial kept as the best Armijo point while the search goes
+//    on: saved to xb, gb before xt is overwritten (gt is overwritten by the
+//    evaluation that follows);
+//  - new direction coefficients (after a new iterate or a retry): dir = cg g +
+//    sum_j coef_j h_j (float64, even and odd terms summed separately, in a
+//    fixed order);
+//  - xt = x + a dir (x itself for the level's start evaluation);
+//  - the mean-term sums S_c of xt over both scans (Eq. 1, M; float64, fixed
+//    trees), reduced by the last block into res->msum.
+// Grid (Gx, 6): blockIdx.y is the displacement plane (scan V, component c:
+// plane 3 V + c), so every block has one plane's share and enough blocks
+// run to hide the float64 latency of the direction sums.
+__global__ void __launch_bounds__(kThreads) trial_kernel(const SolveState* __restrict__ S, const HistSet H,
+                                                         const SolveVecs V, EvalResult* res, double* partials,
+                                                         unsigned* counter) {
+  __shared__ const double* hp[kMaxVec];
+  __shared__ double cf[kMaxVec];
+  __shared__ bool is_last;
   const bool init = S->mode == kModeInit;
-  const bool save = S->save_best && !S->branch;
-  const double a = S->a;
-  for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < n; e += (int64_t)gridDim.x * kThreads) {
-    if (save) {
-      xb[e] = xt[e];
-      gb[e] = gt[e];
+  const bool branch = S->branch != 0;
+  const bool moved = S->moved != 0;
+  const bool save = S->save_best && !branch;
+  const bool best = S->restore_best && !S->save_best;
+  const double* xs = best ? V.xb : V.xt;
+  const double* gs = best ? V.gb : V.gt;
+  const double a = S->a, cg = S->cg;
+  const int nc = branch ? S->nc : 0;
+  if (threadIdx.x < nc) {
+    hp[threadIdx.x] = hvec(H, S->hid[threadIdx.x]);
+    cf[threadIdx.x] = S->coef[threadIdx.x];
+  }
+  __syncthreads();
+  const int Gx = gridDim.x, k = blockIdx.y;
+  const int64_t plane = V.plane;
+  double ms = 0.0;
+  for (int64_t p = (int64_t)blockIdx.x * kThreads + threadIdx.x; p < plane; p += (int64_t)Gx * kThreads) {
+    const int64_t e = k * plane + p;
+    double xe, ge = 0.0;
+    if (moved) {
+      xe = xs[e];
+      ge = gs[e];
+      V.x[e] = xe;
+      V.g[e] = ge;
+    } else {
+      xe = V.x[e];
+      if (branch) ge = V.g[e];
     }
-    xt[e] = init ? x[e] : fma(a, dir[e], x[e]);
+    if (save) {
+      V.xb[e] = V.xt[e];
+      V.gb[e] = V.gt[e];
+    }
+    double d;
+    if (branch) {
+      // two interleaved chains (even / odd terms, fixed order) halve the
+      // dependent float64 latency; the history is read-only here
+      double t0 = 0.0, t1 = 0.0;
+      int j = 0;
+      for (; j + 1 < nc; j += 2) {
+        t0 = fma(cf[j], __ldg(hp[j] + e), t0);
+        t1 = fma(cf[j + 1], __ldg(hp[j + 1] + e), t1);
+      }
+      if (j < nc) t0 = fma(cf[j], __ldg(hp[j] + e), t0);
+      d = fma(cg, ge, t0 + t1);
+      V.dir[e] = d;
+    } else {
+      d = V.dir[e];
+    }
+    const double xn = init ? xe : fma(a, d, xe);
+    V.xt[e] = xn;
+    ms += xn;
+  }
+  ms = block_sum1(ms);
+  if (threadIdx.x == 0) partials[k * Gx + blockIdx.x] = ms;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(counter, 1u) == 6u * Gx - 1u);
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  // S_c: planes c and 3 + c, each over its Gx block partials (fixed order)
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int c = 0; c < 3; c++) {
+      double t = 0.0;
+      for (int b = lane; b < Gx; b += 32) t += partials[c * Gx + b] + partials[(3 + c) * Gx + b];
+      t = warp_sum(t);
+      if (lane == 0) res->msum[c] = t;
+    }
+    if (lane == 0) *counter = 0u;
   }
 }
 
-// accepted step: s = xt - x and y = gt - g into the spare buffers; the trial
-// becomes the iterate (also in the init mode); nothing in the retry mode.
-// When the line search ended on its best Armijo point rather than on the last
-// trial, that point (xb, gb) is taken instead -- unless the last trial is
-// itself that point (kept and taken by the same decision).
-__global__ void __launch_bounds__(kThreads) pair_kernel(const SolveState* __restrict__ S, const HistSet H,
-                                                        const double* __restrict__ xt, const double* __restrict__ gt,
-                                                        const double* __restrict__ xb, const double* __restrict__ gb,
-                                                        double* __restrict__ x, double* __restrict__ g, int64_t n) {
-  const int mode = S->mode;
-  if (mode == kModeRetry) return;
+// After the level's loop: the last new iterate (see trial_kernel) becomes x.
+__global__ void __launch_bounds__(kThreads) finish_kernel(const SolveState* __restrict__ S, const SolveVecs V) {
+  if (!S->moved) return;
   const bool best = S->restore_best && !S->save_best;
-  const double* xs = best ? xb : xt;
-  const double* gs = best ? gb : gt;
-  double* sv = H.S[S->spare];
-  double* yv = H.Y[S->spare];
-  const bool pair = mode == kModeAccept;
-  for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < n; e += (int64_t)gridDim.x * kThreads) {
-    const double xn = xs[e], gn = gs[e];
-    if (pair) {
-      sv[e] = xn - x[e];
-      yv[e] = gn - g[e];
-    }
-    x[e] = xn;
-    g[e] = gn;
-  }
+  const double* xs = best ? V.xb : V.xt;
+  for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < V.n; e += (int64_t)gridDim.x * kThreads)
+    V.x[e] = xs[e];
 }
 
 // ---- the compact-form algebra (one thread), after the products are known
@@ -123,7 +199,6 @@ __device__ void history_update(SolveState* S) {
     S->yg[S->cand[t]] = r[2 * (2 * t + 1) + 1];
   }
   S->gg = r[2 * K + 1];
-  S->gmax = r[2 * K + 2];
 }
 
 // Block-wide copy of the solver state, 16 bytes per load, all of a thread's
@@ -147,7 +222,7 @@ __device__ __forceinline__ void copy_state(SolveState* dst, const SolveState* sr
 }
 static_assert(sizeof(SolveState) % 16 == 0, "solver state is copied in 16-byte words");
 
-// After the products: history update, stopping tests, and the compact-form
+// After the products: history update and the compact-form
 // (Byrd, Nocedal & Schnabel) direction dir = -H g with H0 = gamma I, gamma
 // from the newest pair, as coefficients of g and the history vectors; g . dir
 // follows from the products (no extra pass).  Run by every thread of one
@@ -160,30 +235,11 @@ struct Algebra {
   double YY[kMaxM][kMaxM];  // y_i . y_j
   double a[kMaxM], b[kMaxM], u[kMaxM], w[kMaxM], top[kMaxM];
   double rd[kMaxM];         // 1 / R_ii
-  int proceed;
 };
 
 __device__ void after_products(SolveState* S, Algebra& A) {
-  if (threadIdx.x == 0) {
-    const bool accepted = S->mode == kModeAccept;
-    history_update(S);
-    A.proceed = 1;
-    if (accepted && S->small >= 3) {
-      S->status = 0;
-      S->done = 1;
-      A.proceed = 0;
-    } else if (S->iters >= S->max_iter) {
-      S->status = 1;
-      S->done = 1;
-      A.proceed = 0;
-    } else if (S->gmax <= S->gtol) {
-      S->status = 0;
-      S->done = 1;
-      A.proceed = 0;
-    }
-  }
+  if (threadIdx.x == 0) history_update(S);
   __syncthreads();
-  if (!A.proceed) return;
   const int k = S->k;
   for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
     const int i = t / k, j = t % k;
@@ -277,47 +333,64 @@ __device__ __forceinline__ double warp_reduce_scatter32(double* v, int lane) {
   return v[0];
 }
 
-// The products pass over this block's share of the elements: v[2c] += h_c
-// q0 (accepted step only), v[2c+1] += h_c g; v[2 kChunk], v[2 kChunk + 1]:
-// q0 . q0 and g . g (first row only); mx: max |g| as ordered bits.
+// The products pass over this block's share of the elements, with gp the
+// gradient at the iterate the products are for.  After an accepted step the
+// new pair s = xs - x, y = gp - g is formed here; the row whose candidates
+// include it (slots cs, cs + 1) takes them from registers and stores them.  v[2c] += h_c . y (accepted step only), v[2c+1] += h_c .
+// gp; first row: v[2 kChunk] += y . y, v[2 kChunk + 1] += gp . gp.
 template <bool kAccepted>
-__device__ __forceinline__ void dots_pass(const double* const* h, int kn, bool first, const double* __restrict__ q0,
-                                          const double* __restrict__ g, int64_t e0, int64_t e1, double* v,
-                                          unsigned long long& mx) {
+__device__ __forceinline__ void dots_pass(const double* const* h, int kn, int cs, bool first, bool store,
+                                          const double* __restrict__ xs, const double* __restrict__ gp,
+                                          const double* __restrict__ x, const double* __restrict__ g,
+                                          double* __restrict__ sv, double* __restrict__ yv, int64_t e0, int64_t e1,
+                                          double* v) {
+  // Every load here is non-coherent (read-only path): none of these vectors
+  // is written by this kernel except the spare pair buffers, whose loaded
+  // values are discarded for the register copies, so the compiler may batch
+  // the loads of later elements ahead of this element's stores.
   for (int64_t e = e0 + threadIdx.x; e < e1; e += kThreads) {
-    const double gv = g[e];
-    const double v0 = kAccepted ? q0[e] : 0.0;
+    const double gv = __ldg(gp + e);
+    double sn = 0.0, yn = 0.0;
+    if (kAccepted) {
+      sn = __ldg(xs + e) - __ldg(x + e);
+      yn = gv - __ldg(g + e);
+    }
 #pragma unroll
     for (int c = 0; c < kChunk; c++) {
       if (c < kn) {
-        const double hv = h[c][e];
-        if (kAccepted) v[2 * c] = fma(hv, v0, v[2 * c]);
+        double hv = __ldg(h[c] + e);
+        if (kAccepted) hv = (c == cs) ? sn : ((c == cs + 1) ? yn : hv);
+        if (kAccepted) v[2 * c] = fma(hv, yn, v[2 * c]);
         v[2 * c + 1] = fma(hv, gv, v[2 * c + 1]);
       }
     }
     if (first) {
-      if (kAccepted) v[2 * kChunk] = fma(v0, v0, v[2 * kChunk]);
+      if (kAccepted) v[2 * kChunk] = fma(yn, yn, v[2 * kChunk]);
       v[2 * kChunk + 1] = fma(gv, gv, v[2 * kChunk + 1]);
-      mx = max(mx, abs_bits(gv));
+    }
+    if (kAccepted && store) {
+      sv[e] = sn;
+      yv[e] = yn;
     }
   }
 }
 
 // Products of the candidate history vectors (the stored pairs and, after an
 // accepted step, the new one) with the probes y_new (accepted step only) and
-// g; g . g and max|g|.  Grid (G, rows): G blocks (one per SM) split the
+// the gradient; g . g.  Grid (G, rows): G blocks (one per SM) split the
 // elements into contiguous shares, rows cover the problem's longest history
 // (block (bx, r) takes candidates r*20 .. r*20+19; rows beyond this step's
 // candidates only arrive).  Within a block the float64 partial sums go
 // through the reduce-scatter above and a fixed sum over the warps; the last
 // block to finish adds the block partials (fixed order) and runs the algebra.
-__global__ void __launch_bounds__(kThreads, 1) dots_kernel(SolveState* S, const HistSet H, const double* __restrict__ g,
-                                                           int64_t n, double* partials, unsigned* counter) {
+__global__ void __launch_bounds__(kThreads, 1) dots_kernel(SolveState* S, const HistSet H, const SolveVecs V,
+                                                           double* partials, unsigned* counter) {
   __shared__ double sm[kVals * kWarps];
-  __shared__ unsigned long long smx[kWarps];
   __shared__ bool is_last;
   const int G = gridDim.x;
-  const bool accepted = S->mode == kModeAccept;
+  const int64_t n = V.n;
+  const int mode = S->mode;
+  const bool accepted = mode == kModeAccept;
   const int nstored = S->k;
   const int ncand = nstored + (accepted ? 1 : 0);
   const int K = 2 * ncand;
@@ -348,22 +421,25 @@ __global__ void __launch_bounds__(kThreads, 1) dots_kernel(SolveState* S, const 
   double v[kVals];
 #pragma unroll
   for (int c = 0; c < kVals; c++) v[c] = 0.0;
-  unsigned long long mx = 0ull;
-  if (accepted) dots_pass<true>(h, kn, first, H.Y[S->spare], g, e0, e1, v, mx);
-  else dots_pass<false>(h, kn, first, nullptr, g, e0, e1, v, mx);
+  // the iterate the products are for: the new one (the last trial, or the
+  // saved best point), or the current one after a retry
+  const bool best = S->restore_best && !S->save_best;
+  const double* xs = best ? V.xb : V.xt;
+  const double* gp = (mode == kModeRetry) ? V.g : (best ? V.gb : V.gt);
+  if (accepted) {
+    const int cs = 2 * nstored - k0;  // the new pair's slots in this row (even: both or neither)
+    const bool store = cs >= 0 && cs < kn;  // the one row holding them stores the pair
+    dots_pass<true>(h, kn, cs, first, store, xs, gp, V.x, V.g, H.S[S->spare], H.Y[S->spare], e0, e1, v);
+  } else {
+    dots_pass<false>(h, kn, -1, first, false, nullptr, gp, nullptr, nullptr, nullptr, nullptr, e0, e1, v);
+  }
   // warp totals: lane i holds values i and 32 + i
   const double t0 = warp_reduce_scatter32(v, lane);
   const double t1 = warp_reduce_scatter32(v + 32, lane);
   sm[lane * kWarps + warp] = t0;
   sm[(32 + lane) * kWarps + warp] = t1;
-  if (first) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) smx[warp] = mx;
-  }
   __syncthreads();
-  // block partials, outputs: [2v] = h_v . q0, [2v+1] = h_v . g, [2K] = q0 . q0,
-  // [2K+1] = g . g, [2K+2] = max|g|
+  // block partials, outputs: [2v] = h_v . y, [2v+1] = h_v . g, [2K] = y . y, [2K+1] = g . g
   const int t = threadIdx.x;
   int out = -1;
   if (t < 2 * kn) out = 2 * k0 + t;
@@ -373,11 +449,6 @@ __global__ void __launch_bounds__(kThreads, 1) dots_kernel(SolveState* S, const 
     double a = 0.0;
     for (int w = 0; w < kWarps; w++) a += sm[t * kWarps + w];
     partials[(int64_t)out * G + blockIdx.x] = a;
-  }
-  if (first && t == kThreads - 1) {
-    unsigned long long m = 0ull;
-    for (int w = 0; w < kWarps; w++) m = max(m, smx[w]);
-    partials[(int64_t)(2 * K + 2) * G + blockIdx.x] = __longlong_as_double((long long)m);
   }
   __threadfence();
   __syncthreads();
@@ -391,20 +462,12 @@ __global__ void __launch_bounds__(kThreads, 1) dots_kernel(SolveState* S, const 
   __shared__ SolveState sS;
   copy_state(&sS, S);
   __syncthreads();
-  const int nout = 2 * K + 3;
+  const int nout = 2 * K + 2;
   for (int o = warp; o < nout; o += kWarps) {
-    const bool is_max = (o == nout - 1);
     double a = 0.0;
-    unsigned long long m = 0ull;
-    for (int bx = lane; bx < G; bx += 32) {
-      const double u = partials[(int64_t)o * G + bx];
-      if (is_max) m = max(m, (unsigned long long)__double_as_longlong(u));
-      else a += u;
-    }
+    for (int bx = lane; bx < G; bx += 32) a += partials[(int64_t)o * G + bx];
     a = warp_sum(a);
-#pragma unroll
-    for (int s = 16; s > 0; s >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, s));
-    if (lane == 0) sS.dots[o] = is_max ? __longlong_as_double((long long)m) : a;
+    if (lane == 0) sS.dots[o] = a;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -417,33 +480,6 @@ __global__ void __launch_bounds__(kThreads, 1) dots_kernel(SolveState* S, const 
   after_products(&sS, alg);
   __syncthreads();
   copy_state(S, &sS);
-}
-
-// dir = cg g + sum_j coef_j h_j (float64, terms in a fixed order)
-__global__ void __launch_bounds__(kThreads) comb_kernel(const SolveState* __restrict__ S, const HistSet H,
-                                                        const double* __restrict__ g, double* __restrict__ dir,
-                                                        int64_t n) {
-  __shared__ const double* hp[kMaxVec];
-  __shared__ double cf[kMaxVec];
-  if (S->done) return;
-  const int nc = S->nc;
-  const double cg = S->cg;
-  if (threadIdx.x < nc) {
-    hp[threadIdx.x] = hvec(H, S->hid[threadIdx.x]);
-    cf[threadIdx.x] = S->coef[threadIdx.x];
-  }
-  __syncthreads();
-  for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < n; e += (int64_t)gridDim.x * kThreads) {
-    double s = 0.0;
-    for (int j = 0; j < nc; j++) s = fma(cf[j], hp[j][e], s);
-    dir[e] = fma(cg, g[e], s);
-  }
-}
-
-// continues the level's loop while it is not done (hard cap on evaluations)
-__global__ void loop_kernel(const SolveState* __restrict__ S, cudaGraphConditionalHandle h_while) {
-  const bool more = !S->done && S->evals < S->max_evals + 2;
-  cudaGraphSetConditional(h_while, more ? 1u : 0u);
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -473,8 +509,8 @@ __global__ void level_init_kernel(SolveState* S, const EvalResult* __restrict__ 
   S->done = 0;
   S->status = 1;
   S->iters = S->evals = S->small = S->retried = S->ls = S->have_lo = 0;
-  S->save_best = S->restore_best = S->branch = 0;
-  S->f = S->ft = S->fb = S->dg0 = S->a = S->lo = 0.0;
+  S->save_best = S->restore_best = S->branch = S->moved = 0;
+  S->f = S->ft = S->fb = S->dg0 = S->a = S->lo = S->gmaxb = 0.0;
   S->hi = INFINITY;
   S->eta = eta;
   S->k = 0;
@@ -524,29 +560,22 @@ int device_sm_count() {
   return sms;
 }
 
-cudaError_t launch_solve_trial(const SolveState* S, const double* x, const double* dir, double* xt, const double* gt,
-                               double* xb, double* gb, int64_t n, cudaStream_t s) {
-  trial_kernel<<<grid_for(n), kThreads, 0, s>>>(S, x, dir, xt, gt, xb, gb, n);
+cudaError_t launch_solve_trial(SolveState* S, const HistSet& H, const SolveVecs& V, EvalResult* res, double* partials,
+                               unsigned* counter, cudaStream_t s) {
+  trial_kernel<<<dim3(grid_for(V.plane), 6), kThreads, 0, s>>>(S, H, V, res, partials, counter);
   return cudaGetLastError();
 }
 
-cudaError_t launch_solve_pair(const SolveState* S, const HistSet& H, const double* xt, const double* gt,
-                              const double* xb, const double* gb, double* x, double* g, int64_t n, cudaStream_t s) {
-  pair_kernel<<<grid_for(n), kThreads, 0, s>>>(S, H, xt, gt, xb, gb, x, g, n);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_solve_dots(SolveState* S, const HistSet& H, int m, const double* g, int64_t n, double* partials,
+cudaError_t launch_solve_dots(SolveState* S, const HistSet& H, int m, const SolveVecs& V, double* partials,
                               unsigned* counter, cudaStream_t s) {
   if (m < 1 || m > kMaxM) return cudaErrorInvalidValue;
   const int rows = (2 * (m + 1) + kChunk - 1) / kChunk;
-  dots_kernel<<<dim3(solve_dots_blocks(n), rows), kThreads, 0, s>>>(S, H, g, n, partials, counter);
+  dots_kernel<<<dim3(solve_dots_blocks(V.n), rows), kThreads, 0, s>>>(S, H, V, partials, counter);
   return cudaGetLastError();
 }
 
-cudaError_t launch_solve_comb(const SolveState* S, const HistSet& H, const double* g, double* dir, int64_t n,
-                              cudaStream_t s) {
-  comb_kernel<<<grid_for(n), kThreads, 0, s>>>(S, H, g, dir, n);
+cudaError_t launch_solve_finish(const SolveState* S, const SolveVecs& V, cudaStream_t s) {
+  finish_kernel<<<grid_for(V.n), kThreads, 0, s>>>(S, V);
   return cudaGetLastError();
 }
 
@@ -560,9 +589,6 @@ cudaError_t launch_solve_level_stats(const SolveState* S, LevelStatsDev* out, cu
   return cudaGetLastError();
 }
 
-cudaError_t launch_solve_loop(const SolveState* S, cudaGraphConditionalHandle h_while, cudaStream_t s) {
-  loop_kernel<<<1, 1, 0, s>>>(S, h_while);
-  return cudaGetLastError();
-}
+
 
 }  // namespace octmc

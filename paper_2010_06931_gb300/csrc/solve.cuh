@@ -21,17 +21,28 @@ namespace octmc {
 // The controller fields are read once (independent loads) and written back
 // once: this runs in a single thread on state in global memory, where every
 // dependent access would cost a round trip to L2.
-__device__ __forceinline__ void ls_decide(SolveState* S, double ft, double dgt, cudaGraphConditionalHandle h_branch) {
-  const int mode0 = S->mode, max_ls = S->max_ls, max_evals = S->max_evals, k0 = S->k;
+//
+// ft, dgt: f and grad . dir at the trial; gmaxt: max |grad| at the trial.
+// Once a new iterate is taken (the start point, or an accepted step) the
+// stopping tests run here: 3 iterations in a row with relative decrease
+// below ftol (status 0), max_iter iterations (status 1), max |grad| <= gtol
+// at the new iterate (status 0).  h_branch runs the accepted-step branch
+// (history and direction) when the level goes on from a new iterate or a
+// retry; h_while continues the level's loop.
+__device__ __forceinline__ void ls_decide(SolveState* S, double ft, double dgt, double gmaxt,
+                                          cudaGraphConditionalHandle h_branch,
+                                          cudaGraphConditionalHandle h_while) {
+  const int mode0 = S->mode, max_ls = S->max_ls, max_evals = S->max_evals, k0 = S->k, max_iter = S->max_iter;
   int ls = S->ls, evals = S->evals + 1, have_lo = S->have_lo, retried = S->retried;
   int iters = S->iters, small = S->small, status = S->status, done = S->done, mode = mode0, k = k0;
-  double f = S->f, fb = S->fb, a = S->a, lo = S->lo, hi = S->hi;
-  const double dg0 = S->dg0, ftol = S->ftol;
-  int save_best = 0, restore_best = 0, branch = 0;
-  double ftn = ft;
+  double f = S->f, fb = S->fb, a = S->a, lo = S->lo, hi = S->hi, gmaxb = S->gmaxb;
+  const double dg0 = S->dg0, ftol = S->ftol, gtol = S->gtol;
+  int save_best = 0, restore_best = 0, branch = 0, moved = 0;
+  double ftn = ft, gmax_new = gmaxt;
   if (mode0 == kModeInit) {
     f = ft;
     branch = 1;
+    moved = 1;
   } else {
     ls++;
     const double at = a;
@@ -43,6 +54,7 @@ __device__ __forceinline__ void ls_decide(SolveState* S, double ft, double dgt, 
       lo = at;
       have_lo = 1;
       fb = ft;
+      gmaxb = gmaxt;
       save_best = 1;
       a = isinf(hi) ? 2.0 * at : 0.5 * (lo + hi);
     } else {
@@ -55,6 +67,7 @@ __device__ __forceinline__ void ls_decide(SolveState* S, double ft, double dgt, 
         if (have_lo) {
           restore_best = 1;
           ftn = fb;
+          gmax_new = gmaxb;
           accepted = true;
         } else if (k > 0 && !retried) {
           k = 0;  // drop the history, retry from -g
@@ -74,15 +87,30 @@ __device__ __forceinline__ void ls_decide(SolveState* S, double ft, double dgt, 
         small = (rel < ftol) ? small + 1 : 0;
         mode = kModeAccept;
         branch = 1;
+        moved = 1;
       }
+    }
+  }
+  if (moved && !done) {
+    if (mode == kModeAccept && small >= 3) {
+      status = 0;
+      done = 1;
+    } else if (iters >= max_iter) {
+      status = 1;
+      done = 1;
+    } else if (gmax_new <= gtol) {
+      status = 0;
+      done = 1;
     }
   }
   if (evals >= max_evals && !done && branch == 0) {
     status = 2;
     done = 1;
   }
+  if (done) branch = 0;  // nothing more to prepare: the level ends
   S->save_best = save_best;
   S->restore_best = restore_best;
+  S->moved = moved;
   S->evals = evals;
   S->ls = ls;
   S->have_lo = have_lo;
@@ -96,11 +124,13 @@ __device__ __forceinline__ void ls_decide(SolveState* S, double ft, double dgt, 
   S->f = f;
   S->ft = ftn;
   S->fb = fb;
+  S->gmaxb = gmaxb;
   S->a = a;
   S->lo = lo;
   S->hi = hi;
   S->branch = branch;
   cudaGraphSetConditional(h_branch, branch ? 1u : 0u);
+  cudaGraphSetConditional(h_while, (!done && evals < max_evals + 2) ? 1u : 0u);
 }
 
 }  // namespace octmc
