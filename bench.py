@@ -215,7 +215,7 @@ def measured_peaks():
 def data_kernel_sha1():
     """sha1 over the sources that define the data-term kernel."""
     hsh = hashlib.sha1()
-    for f in ("common.cuh", "sample.cuh", "k_data.cu"):
+    for f in ("common.cuh", "sample.cuh", "data.cuh", "k_data.cu"):
         hsh.update(open(os.path.join(ROOT, "paper_2010_06931_gb300", "csrc", f), "rb").read())
     return hsh.hexdigest()
 

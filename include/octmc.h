@@ -83,6 +83,12 @@ typedef struct {
     double gtol;          /* stop when max|grad| <= gtol                               */
     double ftol;          /* stop after 3 iterations of relative decrease < ftol (1e-7) */
     void *stream;         /* cudaStream_t (NULL = the legacy default stream)           */
+    int persistent_ascans;/* levels of at most this many A-scans are solved by one
+                             persistent cooperative kernel (all iterations in one
+                             launch, grid barriers between phases); 0: never
+                             (default: on this GPU the graph-driven loop is faster
+                             at every level size measured).  Problems run by the
+                             server never use it.                                  */
 } octmc_desc;
 
 /* Per-level statistics of a solve. */
@@ -90,7 +96,8 @@ typedef struct {
     int level;            /* pyramid level solved                                      */
     int iters;            /* accepted L-BFGS iterations                                */
     int evals;            /* objective + gradient evaluations                          */
-    int status;           /* 0 converged, 1 iteration cap, 2 line search exhausted     */
+    int status;           /* 0 converged, 1 iteration cap, 2 line search exhausted,
+                             3 a grid barrier of the persistent level kernel timed out */
     double f;             /* final objective                                           */
     double eta;           /* eta used on this level (Eq. 10)                           */
     double seconds;       /* wall time of the level                                    */
@@ -395,6 +402,15 @@ int octmc_data_term_static(const float *sx, const float *sy, const float *ax, co
                            const float *vx, const float *vy, int w, int h, int d, const double *disp,
                            double eta, double delta0, double eps_h, int loss, double *grad_out,
                            double *sums_out, void *stream);
+
+/* Self-test of the bounded grid barrier that the persistent level kernel
+ * (persistent_ascans > 0) waits at between its phases: a cooperative grid of
+ * one block per SM waits once for `extra` (0 or 1) more blocks than it has.
+ * extra = 0: the barrier completes (OK).  extra = 1: it cannot complete, so
+ * every block's wait runs out after its iteration or time limit (about 2 s)
+ * and the call returns TIMEOUT; nothing traps and the context stays usable.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+int octmc_barrier_selftest(int extra);
 
 /* Human-readable name of a return code. */
 const char *octmc_status_string(int code);

@@ -61,7 +61,8 @@ class Problem:
 
     def __init__(self, sx, sy, tx, ty, ax=None, ay=None, vx=None, vy=None, *, storage=F32,
                  alpha=0.1, delta0=0.5, eps_h=1e-3, eps_r=1e-2, mu=0.0, loss=LOSS_PSEUDO_HUBER,
-                 levels=1, lbfgs_m=8, max_iter=5000, max_ls=20, gtol=1e-6, ftol=1e-7):
+                 levels=1, lbfgs_m=8, max_iter=5000, max_ls=20, gtol=1e-6, ftol=1e-7,
+                 persistent_ascans=0):
         L = N.lib()
         arrays = [sx, sy, tx, ty, ax, ay, vx, vy]
         on_dev = all(isinstance(a, torch.Tensor) and a.is_cuda for a in arrays if a is not None)
@@ -81,6 +82,7 @@ class Problem:
         desc.alpha, desc.delta0, desc.eps_h, desc.eps_r, desc.mu = alpha, delta0, eps_h, eps_r, mu
         desc.loss, desc.levels, desc.lbfgs_m = loss, levels, lbfgs_m
         desc.max_iter, desc.max_ls, desc.gtol, desc.ftol = max_iter, max_ls, gtol, ftol
+        desc.persistent_ascans = persistent_ascans
         desc.stream = _stream_ptr().value
         self.levels = levels
         self._h = C.c_void_p()

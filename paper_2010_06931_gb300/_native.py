@@ -25,6 +25,7 @@ class Desc(C.Structure):
         ("eps_r", C.c_double), ("mu", C.c_double), ("loss", C.c_int),
         ("levels", C.c_int), ("lbfgs_m", C.c_int), ("max_iter", C.c_int), ("max_ls", C.c_int),
         ("gtol", C.c_double), ("ftol", C.c_double), ("stream", C.c_void_p),
+        ("persistent_ascans", C.c_int),
     ]
 
 
@@ -49,6 +50,7 @@ _SIGS = {
     "octmc_eval_objective_grad": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_double),
                                             C.c_void_p]),
     "octmc_eval_terms": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
+    "octmc_barrier_selftest": (C.c_int, [C.c_int]),
     "octmc_eval_objective_grad_async": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                                   C.c_void_p]),
     "octmc_eval_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_void_p),

@@ -341,6 +341,10 @@ struct octmc_problem {
   std::map<int, std::pair<cudaGraph_t, cudaGraphExec_t>> graphs;  // solve graphs by (first, last) level
   double* spartials = nullptr;
   unsigned* scounter = nullptr;
+  // the persistent small-level kernel (when persistent_ascans > 0)
+  double* lpart = nullptr;
+  unsigned* lbar = nullptr;  // [2] grid-barrier state, then [2] the error word (as int)
+  int lgrid = 0;
   cudaStream_t cap = nullptr, cap_side = nullptr;
   cudaEvent_t cap_fork = nullptr, cap_join = nullptr;
   unsigned long long* mcounts = nullptr;  // merge: fixed-point density maps [2][h][w]
@@ -385,6 +389,8 @@ struct octmc_problem {
     dfree(lstats);
     dfree(spartials);
     dfree(scounter);
+    dfree(lpart);
+    dfree(lbar);
     if (lstats_host) cudaFreeHost(lstats_host);
     if (cap) cudaStreamDestroy(cap);
     if (cap_side) cudaStreamDestroy(cap_side);
@@ -739,6 +745,13 @@ void ensure_device_solver(octmc_problem* P) {
   P->spartials = dalloc<double>(nout * (size_t)solve_dots_blocks(n0));
   P->scounter = dalloc<unsigned>(1);
   CK(cudaMemsetAsync(P->scounter, 0, sizeof(unsigned), P->st));
+  if (P->desc.persistent_ascans > 0 && P->plane(P->lv.size() - 1) <= P->desc.persistent_ascans) {
+    P->lgrid = level_grid(P->desc.storage);
+    if (P->lgrid > 0) {
+      P->lpart = dalloc<double>((size_t)level_part_doubles(P->lgrid));
+      P->lbar = dalloc<unsigned>(4);
+    }
+  }
   CK(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking));
   CK(cudaStreamCreateWithFlags(&P->cap_side, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&P->cap_fork, cudaEventDisableTiming));
@@ -842,6 +855,37 @@ cudaGraphNode_t append_level(octmc_problem* P, cudaGraph_t g, cudaGraphNode_t de
     CK(launch_solve_level_init(S, P->res, cfg, cs));
     CK(cudaMemsetAsync(P->dir, 0, sizeof(double) * n, cs));
   });
+  SolveVecs V{P->x, P->g, P->xt, P->gt, P->xb, P->gb, P->dir, n, P->plane(l)};
+  if (P->lgrid > 0 && P->plane(l) <= P->desc.persistent_ascans) {
+    // a small level: its whole loop in one cooperative kernel
+    const Level& Lv = P->lv[l];
+    LevelArgs LA;
+    std::memset(&LA, 0, sizeof(LA));
+    LA.S = S;
+    LA.H = H;
+    LA.V = V;
+    LA.D.L = Lv.dev;
+    LA.D.disp = P->xt;
+    LA.D.str_out = P->str;
+    LA.D.ang_out = P->ang;
+    LA.D.grad = P->gdata;
+    LA.D.eta = 1.0;
+    LA.D.eta_dev = &S->eta;
+    LA.D.delta0 = P->have_ang ? D.delta0 : 0.0;
+    LA.D.eps_h = (float)D.eps_h;
+    LA.D.loss = D.loss;
+    LA.alpha = D.alpha;
+    LA.eps_r = D.eps_r;
+    LA.mu = Lv.mu;
+    LA.part = P->lpart;
+    LA.bar = P->lbar;
+    LA.err = reinterpret_cast<int*>(P->lbar + 2);
+    return capture_after(P, g, dep, [&](cudaStream_t cs) {
+      CK(cudaMemsetAsync(P->lbar, 0, 4 * sizeof(unsigned), cs));
+      CK(launch_level_persistent(LA, Lv.dev.dtype, cs));
+      CK(launch_solve_level_stats(S, P->lstats + stats_slot, cs));
+    });
+  }
   // the iteration loop
   cudaGraphConditionalHandle hw, hb;
   CK(cudaGraphConditionalHandleCreate(&hw, g, 1, cudaGraphCondAssignDefault));
@@ -855,7 +899,6 @@ cudaGraphNode_t append_level(octmc_problem* P, cudaGraph_t g, cudaGraphNode_t de
   cudaGraph_t body = wp.conditional.phGraph_out[0];
   CK(cudaGraphConditionalHandleCreate(&hb, body, 0, cudaGraphCondAssignDefault));
   const double* eta_dev = &S->eta;
-  SolveVecs V{P->x, P->g, P->xt, P->gt, P->xb, P->gb, P->dir, n, P->plane(l)};
   const cudaGraphNode_t sink = capture_after(P, body, nullptr, [&](cudaStream_t cs) {
     CK(launch_solve_trial(S, H, V, P->res, P->partials, P->counters + 0, cs));
     capture_eval(P, cs, l, P->xt, P->gt, P->dir, 1.0, eta_dev, D.delta0, S, hb, hw);
@@ -946,7 +989,8 @@ int finish_solve(octmc_problem* P, int first, int last, octmc_stats* st) {
       st[k].seconds = (double)(L.t_end - L.t_start) * 1e-9;
     }
     P->lv[first - k].eta = L.eta;
-    if (!std::isfinite(L.f)) rc = OCTMC_ERR_NONFINITE;
+    if (L.status == 3) rc = OCTMC_ERR_TIMEOUT;
+    else if (!std::isfinite(L.f) && rc != OCTMC_ERR_TIMEOUT) rc = OCTMC_ERR_NONFINITE;
     else if (L.status == 1 && rc == OCTMC_OK) rc = OCTMC_NOT_CONVERGED;
   }
   return rc;
@@ -1276,6 +1320,7 @@ void octmc_desc_defaults(octmc_desc* d) {
   d->max_ls = 20;
   d->gtol = 1e-6;
   d->ftol = 1e-7;
+  d->persistent_ascans = 0;
 }
 
 int octmc_create_problem(const octmc_desc* desc, octmc_problem** out) {
@@ -1284,7 +1329,8 @@ int octmc_create_problem(const octmc_desc* desc, octmc_problem** out) {
   const octmc_desc& D = *desc;
   if (D.w < 1 || D.h < 1 || D.d < 1 || !D.sx || !D.sy || !D.tx || !D.ty) return OCTMC_ERR_INVALID_ARG;
   if ((D.ax == nullptr) != (D.ay == nullptr)) return OCTMC_ERR_INVALID_ARG;
-  if (D.levels < 1 || D.levels > 16 || D.lbfgs_m < 1 || D.lbfgs_m > 32 || D.max_ls < 1 || D.max_iter < 0)
+  if (D.levels < 1 || D.levels > 16 || D.lbfgs_m < 1 || D.lbfgs_m > 32 || D.max_ls < 1 || D.max_iter < 0 ||
+      D.persistent_ascans < 0)
     return OCTMC_ERR_INVALID_ARG;
   if (D.loss != OCTMC_LOSS_PSEUDO_HUBER && D.loss != OCTMC_LOSS_SSD) return OCTMC_ERR_INVALID_ARG;
   if (!(D.eps_h > 0) || !(D.eps_r > 0) || !(D.alpha >= 0) || !(D.delta0 >= 0)) return OCTMC_ERR_INVALID_ARG;
@@ -1628,6 +1674,9 @@ int octmc_server_submit(octmc_server* s, const octmc_desc* desc, int64_t* ticket
   auto r = std::make_shared<octmc_server::Req>();
   r->ticket = s->next_ticket++;
   r->desc = D;
+  // served solves run concurrently on their own streams: a cooperative grid
+  // of one of them would wait for SMs that another holds
+  r->desc.persistent_ascans = 0;
   r->bytes = estimate_bytes_impl(D);
   if (r->bytes > s->budget) return OCTMC_ERR_OOM;  // could never be admitted
   s->queue.push_back(r);
@@ -1680,6 +1729,25 @@ int octmc_server_poll(octmc_server* s, int64_t ticket, int* state, double* disp_
   if (req_rc) *req_rc = r.rc;
   s->all.erase(it);
   s->release(rp);
+  return rc;
+}
+
+int octmc_barrier_selftest(int extra) {
+  if (extra < 0 || extra > 1) return OCTMC_ERR_INVALID_ARG;
+  unsigned* bar = nullptr;
+  if (cudaMalloc(&bar, 4 * sizeof(unsigned)) != cudaSuccess) return OCTMC_ERR_OOM;
+  int rc = OCTMC_OK;
+  int err = 0;
+  if (cudaMemset(bar, 0, 4 * sizeof(unsigned)) != cudaSuccess ||
+      launch_barrier_probe(bar, reinterpret_cast<int*>(bar + 2), extra, 0) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpy(&err, bar + 2, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    rc = OCTMC_ERR_CUDA;
+  } else if (err) {
+    rc = OCTMC_ERR_TIMEOUT;
+  }
+  cudaFree(bar);
   return rc;
 }
 

@@ -394,6 +394,25 @@ cudaError_t launch_solve_trial(SolveState* S, const HistSet& H, const SolveVecs&
 cudaError_t launch_solve_dots(SolveState* S, const HistSet& H, int m, const SolveVecs& V, double* partials,
                               unsigned* counter, cudaStream_t s);
 cudaError_t launch_solve_finish(const SolveState* S, const SolveVecs& V, cudaStream_t s);
+
+// The persistent small-level solve: one cooperative kernel runs the whole
+// loop of a level (k_level.cu).  S holds the level's initial state (from
+// level_init_kernel) on entry and its final state on exit; x the start field
+// on entry and the result on exit.
+struct LevelArgs {
+  SolveState* S;
+  HistSet H;
+  SolveVecs V;
+  DataArgs D;             // the data term at V.xt (eta read through D.eta_dev)
+  double alpha, eps_r, mu;
+  double* part;           // scratch: level_part_doubles(grid) doubles
+  unsigned* bar;          // [2] grid-barrier arrivals and generation, zero on entry
+  int* err;               // 0 on entry; set when a grid barrier times out
+};
+int level_grid(int dtype);              // blocks of the cooperative launch (0: not available)
+int64_t level_part_doubles(int grid);   // scratch size
+cudaError_t launch_level_persistent(const LevelArgs& A, int dtype, cudaStream_t s);
+cudaError_t launch_barrier_probe(unsigned* bar, int* err, int extra, cudaStream_t s);
 int solve_dots_blocks(int64_t n);
 int device_sm_count();  // SMs of the current device (queried once per device)
 cudaError_t launch_solve_level_init(SolveState* S, const EvalResult* res, SolveCfg cfg, cudaStream_t s);

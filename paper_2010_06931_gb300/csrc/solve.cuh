@@ -26,12 +26,10 @@ namespace octmc {
 // Once a new iterate is taken (the start point, or an accepted step) the
 // stopping tests run here: 3 iterations in a row with relative decrease
 // below ftol (status 0), max_iter iterations (status 1), max |grad| <= gtol
-// at the new iterate (status 0).  h_branch runs the accepted-step branch
+// at the new iterate (status 0).  S->branch asks for the accepted-step work
 // (history and direction) when the level goes on from a new iterate or a
-// retry; h_while continues the level's loop.
-__device__ __forceinline__ void ls_decide(SolveState* S, double ft, double dgt, double gmaxt,
-                                          cudaGraphConditionalHandle h_branch,
-                                          cudaGraphConditionalHandle h_while) {
+// retry.
+__device__ __forceinline__ void ls_decide_state(SolveState* S, double ft, double dgt, double gmaxt) {
   const int mode0 = S->mode, max_ls = S->max_ls, max_evals = S->max_evals, k0 = S->k, max_iter = S->max_iter;
   int ls = S->ls, evals = S->evals + 1, have_lo = S->have_lo, retried = S->retried;
   int iters = S->iters, small = S->small, status = S->status, done = S->done, mode = mode0, k = k0;
@@ -129,8 +127,19 @@ __device__ __forceinline__ void ls_decide(SolveState* S, double ft, double dgt, 
   S->lo = lo;
   S->hi = hi;
   S->branch = branch;
-  cudaGraphSetConditional(h_branch, branch ? 1u : 0u);
-  cudaGraphSetConditional(h_while, (!done && evals < max_evals + 2) ? 1u : 0u);
+}
+
+// The level loop goes on while the level is not done (hard cap on evaluations).
+__device__ __forceinline__ bool ls_more(const SolveState* S) { return !S->done && S->evals < S->max_evals + 2; }
+
+// The decision inside the solve graph: the state update, then the IF node's
+// condition (the accepted-step branch) and the WHILE node's (the loop).
+__device__ __forceinline__ void ls_decide(SolveState* S, double ft, double dgt, double gmaxt,
+                                          cudaGraphConditionalHandle h_branch,
+                                          cudaGraphConditionalHandle h_while) {
+  ls_decide_state(S, ft, dgt, gmaxt);
+  cudaGraphSetConditional(h_branch, S->branch ? 1u : 0u);
+  cudaGraphSetConditional(h_while, ls_more(S) ? 1u : 0u);
 }
 
 }  // namespace octmc

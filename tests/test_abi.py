@@ -51,6 +51,18 @@ def test_host_only_calls(lib_path):
     assert L.octmc_create_problem(ctypes.byref(d), ctypes.byref(h)) == -1  # w = h = d = 0
     assert L.octmc_level_shape(None, 0, None, None, None) == -1
     assert L.octmc_eval_objective_grad_async(None, 0, None, None, None, None) == -1
+    assert L.octmc_barrier_selftest(-1) == -1 and L.octmc_barrier_selftest(2) == -1
+    # a negative persistent-level size is rejected before any device work
+    buf = (ctypes.c_float * 8)()
+    tbuf = (ctypes.c_double * 4)()
+    d2 = N.Desc()
+    L.octmc_desc_defaults(ctypes.byref(d2))
+    d2.w = d2.h = 2
+    d2.d = 2
+    d2.sx = d2.sy = ctypes.cast(buf, ctypes.c_void_p)
+    d2.tx = d2.ty = ctypes.cast(tbuf, ctypes.c_void_p)
+    d2.persistent_ascans = -1
+    assert L.octmc_create_problem(ctypes.byref(d2), ctypes.byref(h)) == -1
     assert L.octmc_lbfgs_create(0, 8, None, ctypes.byref(h)) == -1
     # history length 1..32: the dot-product kernel holds 2 (m + 1) <= 66 history vectors
     assert L.octmc_lbfgs_create(100, 0, None, ctypes.byref(h)) == -1

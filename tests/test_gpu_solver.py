@@ -47,3 +47,51 @@ def test_gradient_test_stops_at_the_start_point():
     assert [s["iters"] for s in stc] == [0, 0], stc
     assert float(D.abs().max()) == 0.0
     assert float(np.abs(Dc).max()) == 0.0
+
+
+def clean_c1():
+    return make_config("c1", speckle=False, angio_noise=False, n_saccades=0)
+
+
+def test_persistent_level_kernel_converges_to_the_oracle_minimum():
+    # every level solved by the persistent cooperative kernel (opt-in): the
+    # same algorithm as the graph-driven loop, other reduction orders
+    p, cfg = clean_c1()
+    G, _ = problems(p, levels=3, loss=1, ftol=1e-6, persistent_ascans=1 << 20)
+    D, st = G.solve_full()
+    C = O.OracleProblem(p["sx"], p["sy"], p["tx"], p["ty"], p["ax"], p["ay"], p["vx"], p["vy"], loss=1)
+    Dc, stc = C.solve_full(3, ftol=1e-6)
+    D = D.cpu().numpy()
+    rms = float(np.sqrt(((D - Dc) ** 2).mean()))
+    P0 = C.pyramid(1)[0]
+    P0.eta = stc[-1]["eta"]
+    f_g = P0.eval(D, grad=False)[0]
+    print("persistent levels, clean c1 (SSD): GPU vs oracle %.4f px, FP64 objective %.9g / %.9g, iters %s / %s"
+          % (rms, f_g, stc[-1]["f"], [s["iters"] for s in st], [s["iters"] for s in stc]))
+    assert [s["status"] for s in st] == [0, 0, 0], st
+    assert rms <= 0.05
+    assert f_g <= stc[-1]["f"] * (1.0 + 1e-4)
+
+
+def test_persistent_level_kernel_iteration_cap():
+    p, _ = make_config("c1")
+    G, _ = problems(p, levels=2, max_iter=7, persistent_ascans=1 << 20)
+    D, st = G.solve_full()
+    assert [s["status"] for s in st] == [1, 1], st
+    assert [s["iters"] for s in st] == [7, 7], st
+    assert torch.isfinite(D).all()
+
+
+def test_bounded_grid_barrier_reports_timeout():
+    # a barrier waiting for one block more than the grid has cannot complete:
+    # every wait runs out (about 2 s), the call reports TIMEOUT, nothing
+    # traps, and the device stays usable
+    from paper_2010_06931_gb300 import _native as N
+    L = N.lib()
+    assert L.octmc_barrier_selftest(0) == 0
+    assert L.octmc_barrier_selftest(1) == -5
+    assert L.octmc_barrier_selftest(0) == 0
+    p, _ = make_config("c1")
+    G, C = problems(p)
+    D = torch.zeros(G.disp_shape(0), dtype=torch.float64, device="cuda")
+    assert np.isfinite(G.eval_objective_grad(0, D))
