@@ -31,6 +31,7 @@
 
 #include "common.cuh"
 #include "data.cuh"
+#include "reg_ascan.cuh"
 #include "solve.cuh"
 #include "solve_algebra.cuh"
 
@@ -123,63 +124,8 @@ __device__ unsigned long long lblock_max(unsigned long long v) {
   return v;
 }
 
-// Pseudo-Huber loss of a displacement difference and its derivative (the
-// regulariser's L_epsR, as in the regulariser kernel).
-__device__ __forceinline__ float huber_r(float x, float inv_eps, float* dl) {
-  const float r = x * inv_eps;
-  const float q = fmaf(r, r, 1.0f);
-  const float is = rsqrtf(q);
-  *dl = r * is;
-  return __fdividef(x * r, fmaf(q, is, 1.0f));
-}
-
 __device__ __forceinline__ const double* lhvec(const HistSet& H, int id) {
   return (id & 1) ? H.Y[id >> 1] : H.S[id >> 1];
-}
-
-// One A-scan of the evaluation by one warp: the data term (lanes 0..7 hold
-// its outputs), then lanes 0..5 the regulariser terms, the mean-term
-// gradient and the float64 gradient of component 3 V + c = lane; partial
-// sums into acc (S^str, S^ang, R, grad . dir) and the running max |grad|.
-template <typename T>
-__device__ __forceinline__ void eval_ascan(const LevelArgs& A, int64_t p, int lane, float two_mu_s, float inv_eps_r,
-                                        float alpha_d, double* acc, unsigned long long* gmx) {
-  const SolveVecs& V = A.V;
-  const LevelDev& L = A.D.L;
-  const int64_t plane = V.plane;
-  int base[6];
-  float frac[6];
-  split_displacement(V.xt, plane, p, (int)(p % L.w), (int)(p / L.w), L, lane, base, frac);
-  const float out = data_value<T>(A.D, p, lane, base, frac);
-  // lane 0: the A-scan's structural term, lane 1 its angiographic term,
-  // lane 2 + q: the data-term gradient of component q
-  const float gdat = __shfl_sync(0xffffffffu, out, (lane + 2) & 31);
-  if (lane == 0) acc[0] += widen_exact(out);
-  if (lane == 1) acc[1] += widen_exact(out);
-  if (lane < 6) {
-    const int V_ = lane / 3, c_ = lane % 3;
-    const int nx = L.next[V_][p], pv = L.prev[V_][p];
-    const double* dc = V.xt + (int64_t)(3 * V_ + c_) * plane;
-    const double x = dc[p];
-    float r = 0.f, gr = 0.f;
-    if (nx >= 0) {  // pair (p, next) counted at its first sample
-      float dl;
-      const float wn = L.wnext[V_][p];
-      r = wn * huber_r((float)(dc[nx] - x), inv_eps_r, &dl);  // float64 difference, rounded once
-      gr = fmaf(-wn, dl, gr);
-    }
-    if (pv >= 0) {
-      float dl;
-      huber_r((float)(x - dc[pv]), inv_eps_r, &dl);
-      gr = fmaf(L.wprev[V_][p], dl, gr);
-    }
-    const int64_t gi = (int64_t)(3 * V_ + c_) * plane + p;
-    const double gw = widen_exact(gdat + fmaf(alpha_d, gr, two_mu_s));
-    V.gt[gi] = gw;
-    acc[2] += widen_exact(r);
-    acc[3] = fma(gw, V.dir[gi], acc[3]);  // line-search product in float64
-    *gmx = max(*gmx, (unsigned long long)__double_as_longlong(gw) & 0x7fffffffffffffffull);
-  }
 }
 
 template <typename T>
@@ -279,7 +225,7 @@ __global__ void __launch_bounds__(kLThreads, 1) level_kernel(const __grid_consta
       unsigned long long gmx = 0ull;
       const float two_mu_s = (float)(2.0 * A.mu * s_ms[lane < 6 ? lane % 3 : 0]);
       for (int64_t p = (int64_t)B * kLWarps + warp; p < plane; p += (int64_t)G * kLWarps)
-        eval_ascan<T>(A, p, lane, two_mu_s, inv_eps_r, alpha_d, acc, &gmx);
+        eval_ascan<T>(A.D, V.gt, V.dir, p, lane, two_mu_s, inv_eps_r, alpha_d, acc, &gmx);
       lblock_sum<4>(acc);
       gmx = lblock_max(gmx);
       if (tid == 0) {
