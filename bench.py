@@ -10,9 +10,10 @@ field is reported beside it).  ``value`` times steps issued back to back
 through the asynchronous entry point with inputs resident in GPU memory (as
 the device-resident solver consumes evaluations); ``sync_api`` times the
 synchronous call, which reads f back on the host every step; ``e2e`` times
-that call with the displacement copied in from pinned host memory and the
-gradient copied back every step.  The two volumes (368 MB)
-exceed the 129 MB L2, so every step streams them from HBM.
+steps that copy the displacement in from pinned host memory, evaluate, and
+copy the gradient and the result terms back, with one host wait per step.
+The two volumes (368 MB) exceed the 129 MB L2, so every step streams them
+from HBM.
 
 The solve runs every level to the library's stopping rule (one device
 graph per solve); its result is compared with the FP64 oracle's converged
@@ -440,25 +441,39 @@ def run_ours(args):
     ms = time_evals_async(P, D, G, T, args.steps, stream, barrier)
     ms_truth = time_evals_async(P, Dt, G, T, args.steps, stream, barrier)
 
-    # ---- end to end through host buffers
+    # ---- end to end through host buffers: every step copies the field in,
+    # evaluates, copies the gradient and the result terms (f among them)
+    # back and waits once, through the asynchronous entry point; the same
+    # through the synchronous call (which waits for f itself) beside it
     Dh = D.cpu().pin_memory()
     Gh = torch.empty(G.shape, dtype=G.dtype).pin_memory()
+    Th = torch.empty(6, dtype=torch.float64).pin_memory()
     Dd = torch.empty_like(D)
-    for _ in range(2):
-        Dd.copy_(Dh, non_blocking=True)
-        P.eval_objective_grad(0, Dd, G)
-        Gh.copy_(G, non_blocking=True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    e0.record(stream)
-    for _ in range(args.steps):
-        Dd.copy_(Dh, non_blocking=True)
-        P.eval_objective_grad(0, Dd, G)
-        Gh.copy_(G, non_blocking=True)
-        stream.synchronize()
-    e1.record(stream)
-    barrier()
-    ms_e2e = e0.elapsed_time(e1)
+    Tt = torch.zeros(6, dtype=torch.float64, device="cuda")
+
+    def e2e_steps(n, sync_api):
+        for _ in range(n):
+            Dd.copy_(Dh, non_blocking=True)
+            if sync_api:
+                P.eval_objective_grad(0, Dd, G)
+            else:
+                P.eval_objective_grad_async(0, Dd, G, Tt, stream)
+                Th.copy_(Tt, non_blocking=True)
+            Gh.copy_(G, non_blocking=True)
+            stream.synchronize()
+
+    def time_e2e(sync_api):
+        e2e_steps(2, sync_api)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        e2e_steps(args.steps, sync_api)
+        e1.record(stream)
+        barrier()
+        return e0.elapsed_time(e1)
+
+    ms_e2e = time_e2e(False)
+    ms_e2e_sync = time_e2e(True)
     clk = clocks.stop()
 
     # ---- converged solve per pair (all levels to the stopping rule; one
@@ -513,6 +528,7 @@ def run_ours(args):
     mo = P.merge(Dm, outputs=("merged", "weights", "angio"))
     for _ in range(3):
         P.merge(Dm, out=mo, outputs=tuple(mo))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     e0.record(stream)
     n_merge = 10
@@ -549,7 +565,7 @@ def run_ours(args):
         serving = serve_leg(args, octmc)
 
     # max over ranks
-    ms, ms_e2e = replica_reduce(dist, [ms, ms_e2e], "cuda")
+    ms, ms_e2e, ms_e2e_sync = replica_reduce(dist, [ms, ms_e2e, ms_e2e_sync], "cuda")
     if rank != 0:
         return
     value = replica_value(ws, args.steps, ms)
@@ -586,7 +602,9 @@ def run_ours(args):
                      "at_true_field_evals_per_s": args.steps / (ms_truth_sync / 1e3),
                      "note": "octmc_eval_objective_grad: f read back on the host every step"},
         "e2e": {"value": replica_value(ws, args.steps, ms_e2e), "unit": "evals/s",
-                "h2d_bytes_per_step": int(Dh.numel() * 8), "d2h_bytes_per_step": int(Gh.numel() * 8)},
+                "h2d_bytes_per_step": int(Dh.numel() * 8), "d2h_bytes_per_step": int((Gh.numel() + 6) * 8),
+                "sync_api_value": replica_value(ws, args.steps, ms_e2e_sync),
+                "note": "asynchronous entry point, one host wait per step; sync_api_value: the synchronous call"},
         "gpu_launches": 3 * args.steps,
         "clocks": clk,
         "solve": solve,
