@@ -107,6 +107,45 @@ def time_enface(octmc, w, h, d, e0, e1, stream, barrier, reps=5):
             "note": "saccade validity + en-face projection, host sync per call"}
 
 
+def time_batch(octmc, barrier, reps=20, pairs=16):
+    """Objective + gradient of `pairs` independent 128 x 128 x 256 problems:
+    one batched call (octmc_eval_batch: one launch per kernel for all of
+    them) against as many single synchronous calls.  Both forms wait for
+    their results, so host wall time is what is compared."""
+    import torch
+    from octsynth import make_config
+    p, _ = make_config("c4", device="cuda")
+    probs = [octmc.Problem(p["sx"], p["sy"], p["tx"], p["ty"], p["ax"], p["ay"], p["vx"], p["vy"])
+             for _ in range(pairs)]
+    rng = np.random.default_rng(5)
+    Ds = [torch.from_numpy(rng.normal(0.0, 0.5, probs[0].disp_shape(0))).cuda() for _ in range(pairs)]
+    Gs = [torch.zeros_like(D) for D in Ds]
+    levels = [0] * pairs
+
+    def batched():
+        octmc.eval_batch(probs, levels, Ds, Gs)
+
+    def singles():
+        for P, D, G in zip(probs, Ds, Gs):
+            P.eval_objective_grad(0, D, G)
+
+    out = {}
+    for name, fn in (("batched", batched), ("single_calls", singles)):
+        for _ in range(3):
+            fn()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        out[name] = pairs * reps / (time.perf_counter() - t0)
+    del probs
+    return {"workload": "%d independent pairs of 128x128 A-scans x 256, float32 (the differentiation "
+                        "configuration), objective + gradient" % pairs,
+            "batched_evals_per_s": out["batched"], "single_calls_evals_per_s": out["single_calls"],
+            "speedup": out["batched"] / out["single_calls"],
+            "note": "host wall time; both forms synchronous (octmc_eval_batch vs octmc_eval_objective_grad)"}
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -118,6 +157,7 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-octa", action="store_true", help="skip the en-face projection timing")
     ap.add_argument("--no-storage", action="store_true", help="skip the 16-bit storage timing")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-evaluation timing")
     ap.add_argument("--serve", action="store_true",
                     help="only the serving leg: Poisson arrivals of mixed-size BF16 pairs")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
@@ -554,6 +594,11 @@ def run_ours(args):
             Q.destroy_problem()
             del Q
 
+    # ---- 16 small problems: one batched call against 16 single calls
+    batch16 = None
+    if not args.no_batch:
+        batch16 = time_batch(octmc, barrier)
+
     # ---- angiography preprocessing of one scan of the pair's size (Sec. 2.2, 2.3)
     enf = None
     if not args.no_octa:
@@ -610,6 +655,7 @@ def run_ours(args):
         "solve": solve,
         "serving": serving,
         "storage_16bit": storage or None,
+        "batch16": batch16,
         "prealign": prealign,
         "merge": merge,
         "enface": enf,
