@@ -98,6 +98,21 @@ def test_eval_ragged_shapes(shape):
     compare_eval(p, D, loss=1, alpha=0.3, eps_r=0.2, mu=0.05)
 
 
+@pytest.mark.parametrize("shape", [(11, 13, 128), (6, 7, 256), (5, 9, 233), (4, 6, 117)])
+def test_eval_depth_block_boundaries(shape):
+    # depths just past and inside a block boundary of the depth mapping (blocks of 116
+    # outputs): a last block of 1 output (117, 233), of 12 (128) and of 24 (256); the depth
+    # shifts reach past both ends of the volume, so the edge groups take the edge rule
+    h, w, d = shape
+    p = make_pair(w, h, d, n_layers=4, n_slabs=1, n_saccades=1, max_saccade=2.0, drift_sigma=0.05, seed=6)
+    rng = np.random.default_rng(8)
+    D = rng.normal(0.0, 1.5, (2, 3, h, w))
+    compare_eval(p, D)
+    compare_eval(p, D, loss=1, alpha=0.3, eps_r=0.2, mu=0.05)
+    D[:, 2] = rng.uniform(-d - 12, d + 12, (2, h, w))
+    compare_eval(p, D)
+
+
 def test_eval_far_outside_the_grid():
     # displacements beyond every edge: all taps are edge samples (clamp-to-edge)
     h, w, d = 9, 10, 23
